@@ -1,0 +1,480 @@
+/*
+ * hz_oracle.c -- plain, slow, obviously correct CPU definition of the
+ * block-decomposed Huffman coder of Cloud et al., "Accelerating Lossless Data
+ * Compression with GPUs" (arXiv 1107.1525).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker the GPU library is
+ * compared against.  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no code, header, table or helper
+ * with the CUDA library, and it includes nothing but the C standard library.
+ *
+ * What the paper fixes, and where:
+ *   - Sec. 2 (Huffman Compression): count every distinct symbol of the
+ *     uncompressed data, give frequent symbols short codes; every symbol is
+ *     replaced by its code.
+ *   - Fig. 2: the code of a symbol is its path in the Huffman tree, so its
+ *     length is the depth of its leaf.
+ *   - Sec. 2.1 (Parallel Huffman Compression) and Fig. 3: the uncompressed
+ *     data is cut into blocks holding a constant number of symbols; each block
+ *     is encoded on its own.
+ *   - Sec. 2.1 and Fig. 4: each encoded block starts with an unencoded
+ *     four-byte integer giving its length, found by an extra pass that sums
+ *     the code lengths of the block's symbols; each block is packed out to a
+ *     four-byte boundary, so the per-block overhead is 32 to 63 bits.
+ *   - Sec. 2.1, last paragraph: a parallel decoder builds a table of block
+ *     offsets from the length delimiters and decodes blocks independently.
+ *
+ * Readings taken where the paper is silent (each one is listed in the design
+ * notes of the repository):
+ *   R1 tie-break: nodes are ordered by (weight, id); a leaf's id is its byte
+ *      value, the t-th merged node gets id 256 + t.
+ *   R2 code values: canonical assignment from the lengths (RFC 1951 3.2.2
+ *      convention) instead of left=0/right=1 tree paths; lengths, and so the
+ *      compressed size, are the same.
+ *   R3 the four-byte delimiter counts payload BITS (excluding itself and the
+ *      padding); little-endian.
+ *   R4 codes are written MSB-first into 32-bit words, words stored
+ *      little-endian, padding bits are zero.
+ *   R5 one code table per buffer, stored as 256 code lengths in a container
+ *      header; R6 the block-offset table is stored after that header
+ *      (flags bit 0) -- the decoder still checks it against the delimiters.
+ *   R7 a buffer with a single distinct symbol codes it with length 1, code 0.
+ *   R8 n = 0 gives no blocks and a header-only stream.
+ *   R9 the last block holds the remaining n - (nb-1)*B symbols.
+ *
+ * Container layout (all integers little-endian):
+ *   0   "HZB1"             4   u32 flags (bit 0: block-offset index present)
+ *   8   u64 n              16  u32 B (symbols per block)     20 u32 nb
+ *   24  u8 len[256]        280 u32 word_offset[nb] if flags bit 0
+ *   then the block records back to back, each
+ *       u32 bits_k, ceil(bits_k/32) payload words.
+ *   word_offset[k] is the position of record k, in 32-bit words, counted from
+ *   the first byte after the index.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_ERR_ARG (-1)
+#define OR_ERR_CAPACITY (-2)
+#define OR_ERR_CORRUPT (-3)
+#define OR_ERR_NOMEM (-4)
+
+#define OR_HEADER_BYTES 280u
+#define OR_MAX_LEN 64
+#define OR_MAX_BLOCK (1u << 24)
+#define OR_FLAG_INDEX 1u
+
+/* ---------------------------------------------------------------- helpers */
+
+static void put_u32(uint8_t* p, uint32_t v) {
+  p[0] = (uint8_t)(v & 0xFF);
+  p[1] = (uint8_t)((v >> 8) & 0xFF);
+  p[2] = (uint8_t)((v >> 16) & 0xFF);
+  p[3] = (uint8_t)((v >> 24) & 0xFF);
+}
+
+static uint32_t get_u32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) |
+         ((uint32_t)p[3] << 24);
+}
+
+static void put_u64(uint8_t* p, uint64_t v) {
+  put_u32(p, (uint32_t)(v & 0xFFFFFFFFu));
+  put_u32(p + 4, (uint32_t)(v >> 32));
+}
+
+static uint64_t get_u64(const uint8_t* p) {
+  return (uint64_t)get_u32(p) | ((uint64_t)get_u32(p + 4) << 32);
+}
+
+static uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+/* ------------------------------------------------------- Sec. 2: counting */
+
+/* freq[s] = number of positions i with x[i] == s. */
+void oracle_histogram(const uint8_t* x, uint64_t n, uint64_t* freq) {
+  for (int s = 0; s < 256; ++s) freq[s] = 0;
+  for (uint64_t i = 0; i < n; ++i) freq[x[i]] += 1;
+}
+
+/* ------------------------------------- Sec. 2, Fig. 2: Huffman code lengths */
+
+/*
+ * Direct form of Huffman's construction.  The live set starts with one leaf
+ * per symbol of nonzero frequency.  While more than one node is live, take out
+ * the two smallest nodes under the (weight, id) order of reading R1 and put
+ * back a parent whose weight is their sum.  A symbol's code length is the
+ * depth of its leaf (Fig. 2: one code bit per edge from the root).
+ * Returns OR_OK, or OR_ERR_ARG if a length would exceed 64.
+ */
+int oracle_code_lengths(const uint64_t* freq, uint8_t* len) {
+  uint64_t weight[511];
+  int parent[511];
+  int live[511];
+  int nlive = 0, nnodes = 256;
+  for (int s = 0; s < 256; ++s) {
+    weight[s] = freq[s];
+    parent[s] = -1;
+    len[s] = 0;
+    if (freq[s] > 0) live[nlive++] = s;
+  }
+  if (nlive == 0) return OR_OK;              /* R8 */
+  if (nlive == 1) { len[live[0]] = 1; return OR_OK; } /* R7 */
+  while (nlive > 1) {
+    int pick[2];
+    for (int r = 0; r < 2; ++r) {
+      int best = 0;
+      for (int j = 1; j < nlive; ++j) {
+        int a = live[j], b = live[best];
+        /* ids are node indices: leaves 0..255, merged nodes 256 + t */
+        if (weight[a] < weight[b] || (weight[a] == weight[b] && a < b)) best = j;
+      }
+      pick[r] = live[best];
+      live[best] = live[nlive - 1];
+      nlive -= 1;
+    }
+    int p = nnodes++;
+    weight[p] = weight[pick[0]] + weight[pick[1]];
+    parent[p] = -1;
+    parent[pick[0]] = p;
+    parent[pick[1]] = p;
+    live[nlive++] = p;
+  }
+  for (int s = 0; s < 256; ++s) {
+    if (freq[s] == 0) continue;
+    int depth = 0;
+    for (int v = s; parent[v] >= 0; v = parent[v]) depth += 1;
+    if (depth > OR_MAX_LEN) return OR_ERR_ARG;
+    len[s] = (uint8_t)depth;
+  }
+  return OR_OK;
+}
+
+/*
+ * Two-queue form of the same construction (van Leeuwen's linear-time method):
+ * leaves sorted by (freq, symbol) in one queue, merged nodes appended to a
+ * second queue in creation order.  Merged weights never decrease and merged
+ * ids always increase, so the head of each queue is its (weight, id) minimum;
+ * on equal weight the leaf wins because every leaf id is below 256.
+ * It must give exactly the lengths of oracle_code_lengths().
+ */
+int oracle_code_lengths_two_queue(const uint64_t* freq, uint8_t* len) {
+  int leaves[256];
+  int m = 0;
+  for (int s = 0; s < 256; ++s) {
+    len[s] = 0;
+    if (freq[s] > 0) leaves[m++] = s;
+  }
+  if (m == 0) return OR_OK;
+  if (m == 1) { len[leaves[0]] = 1; return OR_OK; }
+  /* insertion sort by (freq, symbol) */
+  for (int i = 1; i < m; ++i) {
+    int v = leaves[i], j = i - 1;
+    while (j >= 0 && (freq[leaves[j]] > freq[v] ||
+                      (freq[leaves[j]] == freq[v] && leaves[j] > v))) {
+      leaves[j + 1] = leaves[j];
+      j -= 1;
+    }
+    leaves[j + 1] = v;
+  }
+  uint64_t iw[255];
+  int ip[255];      /* parent of merged node t (index into merged nodes) */
+  int lp[256];      /* parent of leaf symbol */
+  int li = 0, qh = 0, qt = 0;
+  for (int t = 0; t < m - 1; ++t) {
+    uint64_t w = 0;
+    for (int r = 0; r < 2; ++r) {
+      int take_leaf;
+      if (li >= m) take_leaf = 0;
+      else if (qh >= qt) take_leaf = 1;
+      else take_leaf = freq[leaves[li]] <= iw[qh];
+      if (take_leaf) { w += freq[leaves[li]]; lp[leaves[li]] = t; li += 1; }
+      else { w += iw[qh]; ip[qh] = t; qh += 1; }
+    }
+    iw[qt] = w;
+    ip[qt] = -1;
+    qt += 1;
+  }
+  /* depth of merged node t: its parent was created later, so walk down from
+     the root (the last merged node) */
+  int depth[255];
+  for (int t = m - 2; t >= 0; --t) depth[t] = (ip[t] < 0) ? 0 : depth[ip[t]] + 1;
+  for (int i = 0; i < m; ++i) {
+    int s = leaves[i];
+    int d = depth[lp[s]] + 1;
+    if (d > OR_MAX_LEN) return OR_ERR_ARG;
+    len[s] = (uint8_t)d;
+  }
+  return OR_OK;
+}
+
+/* --------------------------------------- reading R2: canonical code values */
+
+/*
+ * Kraft check in exact integer arithmetic: sum over symbols of 2^(64-len)
+ * must not exceed 2^64.  Returns 1 when the lengths form a prefix code.
+ */
+static int kraft_ok(const uint8_t* len) {
+  /* accumulate in units of 2^-64 using a 128-bit value split in two words */
+  uint64_t lo = 0, hi = 0;
+  for (int s = 0; s < 256; ++s) {
+    if (len[s] == 0) continue;
+    if (len[s] > OR_MAX_LEN) return 0;
+    uint64_t add = (len[s] == 64) ? 1 : ((uint64_t)1 << (64 - len[s]));
+    uint64_t prev = lo;
+    lo += add;
+    if (lo < prev) hi += 1;
+  }
+  return hi == 0 || (hi == 1 && lo == 0);
+}
+
+/*
+ * Canonical codes: walk the present symbols in (length, symbol) order; the
+ * first gets code 0 and each next one gets (previous + 1) shifted left by the
+ * growth in length.  Returns OR_ERR_ARG when the lengths break Kraft's
+ * inequality (no prefix code exists) or exceed 64.
+ */
+int oracle_canonical_codes(const uint8_t* len, uint64_t* code) {
+  for (int s = 0; s < 256; ++s) code[s] = 0;
+  if (!kraft_ok(len)) return OR_ERR_ARG;
+  uint64_t c = 0;
+  int prev_len = 0, first = 1;
+  for (int l = 1; l <= OR_MAX_LEN; ++l) {
+    for (int s = 0; s < 256; ++s) {
+      if (len[s] != l) continue;
+      if (first) { c = 0; first = 0; }
+      else c = (c + 1) << (l - prev_len);
+      prev_len = l;
+      code[s] = c;
+    }
+  }
+  return OR_OK;
+}
+
+/* ---------------------------- Sec. 2.1, Figs. 3-4: one independent block */
+
+/*
+ * Sec. 2.1: the "additional pass" over an unencoded block: the payload length
+ * of a block is the sum of the code lengths of its symbols.
+ */
+uint64_t oracle_block_bits(const uint8_t* x, uint64_t count, const uint8_t* len) {
+  uint64_t bits = 0;
+  for (uint64_t i = 0; i < count; ++i) bits += len[x[i]];
+  return bits;
+}
+
+/*
+ * Encode one block of `count` symbols into a record: word 0 is the payload
+ * bit count (reading R3), then the codes one bit at a time, MSB first inside
+ * 32-bit words, zero padding to the word boundary (R4).  words[] receives
+ * 1 + ceil(bits/32) words; returns that count, or 0 if cap_words is too small.
+ */
+uint64_t oracle_encode_block(const uint8_t* x, uint64_t count, const uint8_t* len,
+                             const uint64_t* code, uint32_t* words, uint64_t cap_words) {
+  uint64_t bits = oracle_block_bits(x, count, len);
+  uint64_t nwords = 1 + ceil_div(bits, 32);
+  if (nwords > cap_words) return 0;
+  for (uint64_t w = 0; w < nwords; ++w) words[w] = 0;
+  words[0] = (uint32_t)bits;
+  uint32_t* payload = words + 1;
+  uint64_t p = 0;
+  for (uint64_t i = 0; i < count; ++i) {
+    int l = len[x[i]];
+    uint64_t c = code[x[i]];
+    for (int b = l - 1; b >= 0; --b) {
+      if ((c >> b) & 1u) payload[p / 32] |= (uint32_t)1 << (31 - (p % 32));
+      p += 1;
+    }
+  }
+  return nwords;
+}
+
+/* ---------------------------------------------- the whole compressed stream */
+
+/*
+ * Size in bytes of the stream for x under `len` (no data is written):
+ * header, optional index, and per block 4 * (1 + ceil(bits_k / 32)).
+ */
+int oracle_stream_size(const uint8_t* x, uint64_t n, uint32_t B, const uint8_t* len,
+                       uint32_t flags, uint64_t* size) {
+  if (B == 0 || B > OR_MAX_BLOCK || n > 0xFFFFFFFFull) return OR_ERR_ARG;
+  uint64_t nb = ceil_div(n, B);
+  uint64_t total = OR_HEADER_BYTES + ((flags & OR_FLAG_INDEX) ? 4 * nb : 0);
+  for (uint64_t k = 0; k < nb; ++k) {
+    uint64_t lo = k * B, hi = lo + B < n ? lo + B : n;
+    uint64_t bits = oracle_block_bits(x + lo, hi - lo, len);
+    total += 4 * (1 + ceil_div(bits, 32));
+  }
+  *size = total;
+  return OR_OK;
+}
+
+/*
+ * Compress x[0..n) with blocks of B symbols.  `given_len` may be NULL (build
+ * the code from x's histogram, Sec. 2) or a 256-entry length table that must
+ * be a prefix code covering every symbol present in x.  flags: bit 0 writes
+ * the block-offset index.  On OR_ERR_CAPACITY, *out_len holds the size needed.
+ */
+int oracle_compress(const uint8_t* x, uint64_t n, uint32_t B, const uint8_t* given_len,
+                    uint32_t flags, uint8_t* out, uint64_t cap, uint64_t* out_len) {
+  uint8_t len[256];
+  uint64_t code[256];
+  *out_len = 0;
+  if (B == 0 || B > OR_MAX_BLOCK || n > 0xFFFFFFFFull || (flags & ~OR_FLAG_INDEX))
+    return OR_ERR_ARG;
+  if (given_len) {
+    memcpy(len, given_len, 256);
+    uint64_t freq[256];
+    oracle_histogram(x, n, freq);
+    for (int s = 0; s < 256; ++s)
+      if (freq[s] > 0 && len[s] == 0) return OR_ERR_ARG;
+  } else {
+    uint64_t freq[256];
+    oracle_histogram(x, n, freq);
+    int st = oracle_code_lengths(freq, len);
+    if (st != OR_OK) return st;
+  }
+  if (oracle_canonical_codes(len, code) != OR_OK) return OR_ERR_ARG;
+
+  uint64_t size;
+  int st = oracle_stream_size(x, n, B, len, flags, &size);
+  if (st != OR_OK) return st;
+  *out_len = size;
+  if (size > cap) return OR_ERR_CAPACITY;
+
+  uint64_t nb = ceil_div(n, B);
+  memset(out, 0, size);
+  memcpy(out, "HZB1", 4);
+  put_u32(out + 4, flags);
+  put_u64(out + 8, n);
+  put_u32(out + 16, B);
+  put_u32(out + 20, (uint32_t)nb);
+  memcpy(out + 24, len, 256);
+  uint64_t index_at = OR_HEADER_BYTES;
+  uint64_t blocks_at = index_at + ((flags & OR_FLAG_INDEX) ? 4 * nb : 0);
+
+  uint64_t word_off = 0;
+  uint32_t* rec = NULL;
+  uint64_t rec_cap = 0;
+  for (uint64_t k = 0; k < nb; ++k) {
+    uint64_t lo = k * B, hi = lo + B < n ? lo + B : n;
+    uint64_t need = 1 + ceil_div(oracle_block_bits(x + lo, hi - lo, len), 32);
+    if (need > rec_cap) {
+      free(rec);
+      rec = (uint32_t*)malloc(need * sizeof(uint32_t));
+      if (!rec) return OR_ERR_NOMEM;
+      rec_cap = need;
+    }
+    uint64_t got = oracle_encode_block(x + lo, hi - lo, len, code, rec, rec_cap);
+    if (flags & OR_FLAG_INDEX) put_u32(out + index_at + 4 * k, (uint32_t)word_off);
+    for (uint64_t w = 0; w < got; ++w) put_u32(out + blocks_at + 4 * (word_off + w), rec[w]);
+    word_off += got;
+  }
+  free(rec);
+  return OR_OK;
+}
+
+/* ----------------------------------------------------- Sec. 2.1: decoding */
+
+/* Parse and check the container header. */
+int oracle_parse_header(const uint8_t* s, uint64_t s_len, uint64_t* n, uint32_t* flags,
+                        uint32_t* B, uint32_t* nb, uint8_t* len) {
+  if (s_len < OR_HEADER_BYTES || memcmp(s, "HZB1", 4) != 0) return OR_ERR_CORRUPT;
+  *flags = get_u32(s + 4);
+  *n = get_u64(s + 8);
+  *B = get_u32(s + 16);
+  *nb = get_u32(s + 20);
+  memcpy(len, s + 24, 256);
+  if (*flags & ~OR_FLAG_INDEX) return OR_ERR_CORRUPT;
+  if (*B == 0 || *B > OR_MAX_BLOCK || *n > 0xFFFFFFFFull) return OR_ERR_CORRUPT;
+  if ((uint64_t)*nb != ceil_div(*n, *B)) return OR_ERR_CORRUPT;
+  if (!kraft_ok(len)) return OR_ERR_CORRUPT;
+  int present = 0;
+  for (int s2 = 0; s2 < 256; ++s2) present |= len[s2] != 0;
+  if (*n > 0 && !present) return OR_ERR_CORRUPT;
+  return OR_OK;
+}
+
+/*
+ * Decompress a stream.  Blocks are located by walking the length delimiters
+ * (Sec. 2.1: the offset table is built from them); when the stream carries
+ * the index, every entry must agree with that walk.  Each symbol is found one
+ * bit at a time: after reading l bits as the integer v, a code of length l
+ * matches when first[l] <= v < first[l] + count[l] (canonical codes occupy a
+ * contiguous range at each length).  Each block must use exactly its
+ * delimiter's bit count, its padding must be zero and the stream must end with
+ * the last record.  *n_out receives n (also on OR_ERR_CAPACITY).
+ */
+int oracle_decompress(const uint8_t* s, uint64_t s_len, uint8_t* out, uint64_t cap,
+                      uint64_t* n_out) {
+  uint64_t n;
+  uint32_t flags, B, nb;
+  uint8_t len[256];
+  *n_out = 0;
+  int st = oracle_parse_header(s, s_len, &n, &flags, &B, &nb, len);
+  if (st != OR_OK) return st;
+  *n_out = n;
+  if (n > cap) return OR_ERR_CAPACITY;
+
+  uint64_t code[256];
+  oracle_canonical_codes(len, code);
+  /* per length: first code value, how many codes, and the symbols in order */
+  uint64_t first[OR_MAX_LEN + 1];
+  uint64_t count[OR_MAX_LEN + 1];
+  int sorted[256];
+  int start[OR_MAX_LEN + 1];
+  int m = 0;
+  for (int l = 0; l <= OR_MAX_LEN; ++l) { first[l] = 0; count[l] = 0; start[l] = 0; }
+  for (int l = 1; l <= OR_MAX_LEN; ++l) {
+    start[l] = m;
+    for (int sym = 0; sym < 256; ++sym) {
+      if (len[sym] != l) continue;
+      if (count[l] == 0) first[l] = code[sym];
+      count[l] += 1;
+      sorted[m++] = sym;
+    }
+  }
+
+  uint64_t index_at = OR_HEADER_BYTES;
+  uint64_t blocks_at = index_at + ((flags & OR_FLAG_INDEX) ? 4 * (uint64_t)nb : 0);
+  if (blocks_at > s_len) return OR_ERR_CORRUPT;
+  uint64_t word_off = 0;
+  for (uint64_t k = 0; k < nb; ++k) {
+    if (flags & OR_FLAG_INDEX) {
+      if (get_u32(s + index_at + 4 * k) != word_off) return OR_ERR_CORRUPT;
+    }
+    uint64_t rec_at = blocks_at + 4 * word_off;
+    if (rec_at + 4 > s_len) return OR_ERR_CORRUPT;
+    uint64_t bits = get_u32(s + rec_at);
+    uint64_t nwords = ceil_div(bits, 32);
+    if (rec_at + 4 + 4 * nwords > s_len) return OR_ERR_CORRUPT;
+    const uint8_t* payload = s + rec_at + 4;
+    uint64_t lo = k * (uint64_t)B, hi = lo + B < n ? lo + B : n;
+    uint64_t p = 0;
+    for (uint64_t i = lo; i < hi; ++i) {
+      uint64_t v = 0;
+      int l = 0, found = -1;
+      while (found < 0) {
+        if (p >= bits || l >= OR_MAX_LEN) return OR_ERR_CORRUPT;
+        uint32_t word = get_u32(payload + 4 * (p / 32));
+        uint32_t bit = (word >> (31 - (p % 32))) & 1u;
+        v = (v << 1) | bit;
+        l += 1;
+        p += 1;
+        if (count[l] > 0 && v >= first[l] && v - first[l] < count[l])
+          found = sorted[start[l] + (int)(v - first[l])];
+      }
+      out[i] = (uint8_t)found;
+    }
+    if (p != bits) return OR_ERR_CORRUPT;
+    for (uint64_t q = bits; q < 32 * nwords; ++q) {
+      uint32_t word = get_u32(payload + 4 * (q / 32));
+      if ((word >> (31 - (q % 32))) & 1u) return OR_ERR_CORRUPT;
+    }
+    word_off += 1 + nwords;
+  }
+  if (blocks_at + 4 * word_off != s_len) return OR_ERR_CORRUPT;
+  return OR_OK;
+}
