@@ -1,0 +1,226 @@
+/*
+ * hz.h -- C ABI of libhz, a GB300 (sm_103a) implementation of the
+ * block-decomposed Huffman coder of Cloud, Curry, Ward, Skjellum and
+ * Bangalore, "Accelerating Lossless Data Compression with GPUs"
+ * (arXiv 1107.1525).
+ *
+ * Stream format (Sec. 2.1 and Figs. 3-4 of the paper, plus a container the
+ * paper leaves unspecified).  All integers little-endian:
+ *   offset 0    "HZB1"
+ *   offset 4    u32 flags      bit 0: block-offset index present
+ *   offset 8    u64 n          uncompressed bytes
+ *   offset 16   u32 B          symbols (bytes) per block
+ *   offset 20   u32 nb         ceil(n / B)
+ *   offset 24   u8  len[256]   Huffman code length of each byte value (0 = absent)
+ *   offset 280  u32 word_offset[nb]   only if flags bit 0; record k's position
+ *               in 32-bit words from the first byte after the index
+ *   then nb block records back to back.  Record k = u32 bits_k (the payload
+ *   length in bits: the "unencoded four byte integer" of Sec. 2.1), then
+ *   ceil(bits_k / 32) payload words holding the canonical codes of block k's
+ *   symbols in input order, most significant bit first within each word,
+ *   zero-padded to the word boundary (32-63 bits of overhead per block).
+ * Code values are canonical (in (length, byte) order; the first code is 0 and
+ * each next one is (previous + 1) << (growth in length)); lengths are Huffman
+ * leaf depths with ties broken by (weight, id), leaf id = byte value and the
+ * t-th merged node id = 256 + t.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are device pointers (global memory of the context's
+ *     device) owned by the caller; they must stay valid until the work queued
+ *     on `stream` has finished.  Pointers named h_* are host pointers.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that take a stream only enqueue work on it and return at once, unless
+ *     stated otherwise.
+ *   - Argument errors are returned immediately (HZ_ERR_ARG) and enqueue
+ *     nothing.  Errors found on the device (a corrupt stream, an output buffer
+ *     that is too small, a bounded wait that ran out) are recorded in the
+ *     context's device status word and returned by the next hz_sync() on that
+ *     context; kernels never trap.
+ *   - A context is not thread-safe, and its scratch memory is reused by every
+ *     call: calls on one context must be issued from one host thread and run
+ *     in stream order (one stream, or streams ordered by events).
+ *   - Limits: n < 2^32, 1 <= B <= 2^24, code lengths <= 64.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hz_status;
+#define HZ_OK 0
+#define HZ_PENDING 1
+#define HZ_ERR_ARG (-1)
+#define HZ_ERR_CAPACITY (-2)
+#define HZ_ERR_CORRUPT (-3)
+#define HZ_ERR_NOMEM (-4)
+#define HZ_ERR_BUSY (-5)
+#define HZ_ERR_TIMEOUT (-6)
+#define HZ_ERR_CUDA (-7)
+
+#define HZ_HEADER_BYTES 280u
+#define HZ_MAX_BLOCK (1u << 24)
+#define HZ_MAX_CODE_LEN 64
+
+typedef struct hz_ctx hz_ctx;
+
+/* Code table in host memory: len[s] is the code length of byte value s
+ * (0 = not coded), code[s] its canonical code value in the low len[s] bits. */
+typedef struct {
+  uint8_t len[256];
+  uint64_t code[256];
+} hz_codes;
+
+/*
+ * Create a context on CUDA device `device`.  The context owns its device
+ * scratch (status word, histogram, code table, scan state, decode tables),
+ * grown on demand.  mem_budget_bytes bounds the device memory that
+ * hz_submit() may have admitted at once (0 = no limit).
+ * Returns HZ_ERR_ARG for a bad device, HZ_ERR_NOMEM / HZ_ERR_CUDA on failure.
+ */
+hz_status hz_create(hz_ctx** ctx, int device, uint64_t mem_budget_bytes);
+
+/* Wait for the context's work and free everything it owns.  NULL is a no-op. */
+void hz_destroy(hz_ctx* ctx);
+
+/*
+ * Worst-case stream size in bytes for n input bytes in blocks of block_size
+ * symbols, when the code is built from the same data (Sec. 2: a Huffman code
+ * never averages more than 8 bits per byte, and Sec. 2.1: each block adds
+ * 32-63 bits): 280 + 4*nb (index) + 8*nb + 4*ceil(n/4) + 4*nb.
+ * block_size 0 means the context's automatic choice is not known yet; the
+ * bound then assumes 1-byte blocks.  Returns 0 for n >= 2^32.
+ */
+uint64_t hz_compress_bound(uint64_t n, uint32_t block_size);
+
+/*
+ * Sec. 2 ("counting the appearance of every distinct symbol", then the
+ * Huffman code of Fig. 2): histogram d_in[0..n) on the GPU and build its code.
+ * Writes the lengths and canonical codes to *codes_out (host memory).
+ * Synchronous: returns after the table has reached the host.
+ */
+hz_status hz_build_codes(hz_ctx* ctx, const uint8_t* d_in, uint64_t n, hz_codes* codes_out,
+                         void* stream);
+
+/*
+ * Sec. 2.1: compress d_in[0..n) into the stream format above, in blocks of
+ * block_size symbols (0 = the context's autotuned choice for this size).
+ * codes == NULL builds the code from d_in's histogram (Sec. 2); otherwise
+ * codes->len is used (it must satisfy Kraft's inequality and give every byte
+ * present in d_in a nonzero length; codes->code must be the canonical values
+ * for those lengths, else HZ_ERR_ARG).  d_out receives the stream (capacity
+ * out_cap bytes); *d_out_len (a device u64) receives its size, or the size
+ * that would be needed when out_cap is too small (then hz_sync() reports
+ * HZ_ERR_CAPACITY and d_out holds no valid stream).
+ * Asynchronous on `stream`; device errors surface through hz_sync().
+ */
+hz_status hz_compress(hz_ctx* ctx, const uint8_t* d_in, uint64_t n, uint32_t block_size,
+                      const hz_codes* codes, uint8_t* d_out, uint64_t out_cap,
+                      uint64_t* d_out_len, void* stream);
+
+/*
+ * Sec. 2.1, last paragraph: decode a stream d_in[0..in_len) whose blocks are
+ * located through the offset table (read from the index when flags bit 0 is
+ * set, rebuilt from the length delimiters otherwise) and decoded
+ * independently.  The stream must end exactly at its last record.  d_out
+ * receives n bytes (capacity out_cap); *d_out_len (device u64) receives n.
+ * A stream that fails any check (magic, header fields, Kraft inequality,
+ * index vs. delimiters, a code that does not decode, a block that does not
+ * use exactly bits_k bits, nonzero padding) is reported as HZ_ERR_CORRUPT by
+ * hz_sync(); out_cap < n as HZ_ERR_CAPACITY.  The host reads nothing of the
+ * stream: the header is parsed on the device, so the call never blocks.
+ * Asynchronous on `stream`.
+ */
+hz_status hz_decompress(hz_ctx* ctx, const uint8_t* d_in, uint64_t in_len, uint8_t* d_out,
+                        uint64_t out_cap, uint64_t* d_out_len, void* stream);
+
+/*
+ * Wait for `stream`, then return and clear the context's device status:
+ * HZ_OK, or the first error a kernel recorded since the last hz_sync().
+ */
+hz_status hz_sync(hz_ctx* ctx, void* stream);
+
+/*
+ * Host-buffer round trips (the end-to-end path of Sec. 4, "sans memory
+ * transfer" vs. total throughput): copy h_in to the device, run
+ * hz_compress / hz_decompress there on `stream`, copy the result back to
+ * h_out and synchronise.  *out_len receives the result size (or the size
+ * needed, with HZ_ERR_CAPACITY).  h_in / h_out should be pinned
+ * (cudaHostAlloc / cudaHostRegister) for full copy bandwidth.
+ */
+hz_status hz_compress_host(hz_ctx* ctx, const uint8_t* h_in, uint64_t n, uint32_t block_size,
+                           uint8_t* h_out, uint64_t out_cap, uint64_t* out_len, void* stream);
+hz_status hz_decompress_host(hz_ctx* ctx, const uint8_t* h_in, uint64_t in_len, uint8_t* h_out,
+                             uint64_t out_cap, uint64_t* out_len, void* stream);
+
+/* ------------------------------------------------------------- options */
+#define HZ_OPT_INDEX 1        /* 1 (default): write the block-offset index */
+#define HZ_OPT_PROFILE 2      /* 1: time every kernel launch with CUDA events */
+#define HZ_OPT_DECODE_LUT_BITS 3  /* decode table width W, 8..12 (default 11) */
+#define HZ_OPT_DECODE_THREADS 4   /* threads per decode CTA: 128, 256 or 512 */
+#define HZ_OPT_AUTOTUNE 5     /* 1 (default): block_size 0 picks the tuned size */
+
+/* Set an option; HZ_ERR_ARG for an unknown key or value. */
+hz_status hz_set_option(hz_ctx* ctx, int key, int64_t value);
+int64_t hz_get_option(hz_ctx* ctx, int key);
+
+/* ------------------------------------------------------ instrumentation */
+/* Number of kernels this context has launched since creation. */
+uint64_t hz_launch_count(hz_ctx* ctx);
+
+/*
+ * With HZ_OPT_PROFILE on, every kernel launch is bracketed by CUDA events on
+ * its stream.  hz_profile_read() waits for them, writes up to `max` records
+ * (kernel name id, milliseconds) and clears the log; it returns the number of
+ * records written.  hz_kernel_name() maps an id to a static string.
+ */
+int hz_profile_read(hz_ctx* ctx, int32_t* ids, float* ms, int max);
+const char* hz_kernel_name(int32_t id);
+
+/* ------------------------------------------- batching and serving (a10, a11) */
+/*
+ * One request of a batch: op 0 = compress d_src[0..src_len) in blocks of
+ * block_size (0 = tuned) with a code built from that buffer, op 1 =
+ * decompress the stream d_src[0..src_len).  d_dst (capacity dst_cap) receives
+ * the result.
+ */
+typedef struct {
+  int32_t op;
+  uint32_t block_size;
+  const uint8_t* d_src;
+  uint64_t src_len;
+  uint8_t* d_dst;
+  uint64_t dst_cap;
+} hz_request;
+
+#define HZ_OP_COMPRESS 0
+#define HZ_OP_DECOMPRESS 1
+
+/*
+ * Queue `count` requests as one batch and return at once with a ticket.
+ * Batches are admitted in order against the context's device-memory budget
+ * and run on the context's own stream, every request of a batch inside one
+ * persistent kernel per phase.  HZ_ERR_BUSY if the batch alone exceeds the
+ * budget; HZ_ERR_ARG for a malformed request.
+ */
+hz_status hz_submit(hz_ctx* ctx, const hz_request* reqs, uint32_t count, uint64_t* ticket_out);
+
+/*
+ * Wait up to timeout_ns (0 = just look, < 0 = forever) for batch `ticket`.
+ * HZ_PENDING if it has not finished; otherwise HZ_OK and, per request,
+ * per_req[i] (its status) and out_lens[i] (result bytes), both host arrays
+ * of the batch's length (either may be NULL).  A ticket can be polled to
+ * completion once.
+ */
+hz_status hz_poll(hz_ctx* ctx, uint64_t ticket, int64_t timeout_ns, hz_status* per_req,
+                  uint64_t* out_lens);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HZ_H */

@@ -1,0 +1,487 @@
+// hz_api.cu -- the exported C ABI of libhz (declared in include/hz.h): the
+// context, argument checks, kernel launch sequences, device status, profiling
+// and the host-buffer round trips.
+#include <stdlib.h>
+#include <string.h>
+
+#include <chrono>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "hz_batch.h"
+#include "hz_internal.cuh"
+
+using namespace hz;
+
+struct ProfRec {
+  int32_t id;
+  cudaEvent_t a, b;
+};
+
+struct hz_ctx {
+  int device = 0;
+  int num_sms = 0;
+  uint64_t mem_budget = 0;
+  DevState* d_state = nullptr;
+  DecTables* d_dec = nullptr;
+  TileStatus* d_tiles = nullptr;
+  uint32_t tiles_cap = 0;
+  uint32_t epoch = 0;
+  uint32_t* d_chase = nullptr;
+  uint32_t chase_cap = 0;
+  uint32_t* h_err = nullptr;  // pinned readback of the status words
+  hz_codes* h_codes = nullptr;
+  // staging for the host-buffer round trips
+  uint8_t* d_hin = nullptr;
+  uint64_t d_hin_cap = 0;
+  uint8_t* d_hout = nullptr;
+  uint64_t d_hout_cap = 0;
+  uint64_t* d_len = nullptr;
+  uint64_t* h_len = nullptr;
+  // options
+  int opt_index = 1;
+  int opt_profile = 0;
+  int opt_lut_bits = 11;
+  int opt_dec_threads = 256;
+  int opt_autotune = 1;
+  uint64_t launches = 0;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  BatchState* batch = nullptr;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cudaEvent_t take_event(hz_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Bracket one launch with profile events (when enabled) and count it.
+template <class F>
+hz_status launch(hz_ctx* c, int32_t id, cudaStream_t s, F&& f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->opt_profile) {
+    a = take_event(c);
+    b = take_event(c);
+    cudaEventRecord(a, s);
+  }
+  cudaError_t e = f();
+  if (c->opt_profile) {
+    cudaEventRecord(b, s);
+    c->prof.push_back({id, a, b});
+  }
+  c->launches += 1;
+  return e == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;
+}
+
+hz_status grow(void** p, uint64_t* cap, uint64_t need) {
+  if (need <= *cap) return HZ_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, need) != cudaSuccess) {
+    cudaGetLastError();
+    return HZ_ERR_NOMEM;
+  }
+  *cap = need;
+  return HZ_OK;
+}
+
+uint32_t autotuned_block(hz_ctx* c, uint64_t n) {
+  (void)c;
+  return hz_batch_tuned_block_size(n);
+}
+
+}  // namespace
+
+extern "C" {
+
+hz_status hz_create(hz_ctx** out, int device, uint64_t mem_budget_bytes) {
+  if (!out) return HZ_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return HZ_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return HZ_ERR_ARG;
+  DeviceGuard g(device);
+  hz_ctx* c = new hz_ctx();
+  c->device = device;
+  c->mem_budget = mem_budget_bytes;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  bool ok = cudaMalloc(&c->d_state, sizeof(DevState)) == cudaSuccess &&
+            cudaMalloc(&c->d_dec, dec_tables_bytes()) == cudaSuccess &&
+            cudaMalloc(&c->d_len, sizeof(uint64_t)) == cudaSuccess &&
+            cudaHostAlloc(&c->h_err, 4 * sizeof(uint32_t), cudaHostAllocDefault) == cudaSuccess &&
+            cudaHostAlloc(&c->h_codes, sizeof(hz_codes), cudaHostAllocDefault) == cudaSuccess &&
+            cudaHostAlloc(&c->h_len, sizeof(uint64_t), cudaHostAllocDefault) == cudaSuccess;
+  if (ok) ok = cudaMemset(c->d_state, 0, sizeof(DevState)) == cudaSuccess;
+  if (ok) {
+    // streams without a stored index need a rebuilt offset table
+    c->chase_cap = 1u << 20;
+    ok = cudaMalloc(&c->d_chase, 4ull * c->chase_cap) == cudaSuccess;
+  }
+  if (ok) ok = cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    hz_destroy(c);
+    return HZ_ERR_NOMEM;
+  }
+  c->batch = hz_batch_create(c->device, c->num_sms, mem_budget_bytes);
+  *out = c;
+  return HZ_OK;
+}
+
+void hz_destroy(hz_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  if (c->batch) hz_batch_destroy(c->batch);
+  for (auto& r : c->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  cudaFree(c->d_state);
+  cudaFree(c->d_dec);
+  cudaFree(c->d_tiles);
+  cudaFree(c->d_chase);
+  cudaFree(c->d_hin);
+  cudaFree(c->d_hout);
+  cudaFree(c->d_len);
+  cudaFreeHost(c->h_err);
+  cudaFreeHost(c->h_codes);
+  cudaFreeHost(c->h_len);
+  delete c;
+}
+
+uint64_t hz_compress_bound(uint64_t n, uint32_t block_size) {
+  if (n > 0xFFFFFFFFull) return 0;
+  const uint64_t B = block_size ? block_size : 1;
+  const uint64_t nb = (n + B - 1) / B;
+  // header + index + per block (delimiter + up to 2 partial words) + at most 8 bits per byte
+  return kHeaderBytes + 4 * nb + 12 * nb + 4 * ((n + 3) / 4);
+}
+
+hz_status hz_set_option(hz_ctx* c, int key, int64_t v) {
+  if (!c) return HZ_ERR_ARG;
+  switch (key) {
+    case HZ_OPT_INDEX:
+      if (v != 0 && v != 1) return HZ_ERR_ARG;
+      c->opt_index = (int)v;
+      return HZ_OK;
+    case HZ_OPT_PROFILE:
+      if (v != 0 && v != 1) return HZ_ERR_ARG;
+      c->opt_profile = (int)v;
+      return HZ_OK;
+    case HZ_OPT_DECODE_LUT_BITS:
+      if (v < kLutMinBits || v > kLutMaxBits) return HZ_ERR_ARG;
+      c->opt_lut_bits = (int)v;
+      return HZ_OK;
+    case HZ_OPT_DECODE_THREADS:
+      if (v != 128 && v != 256 && v != 512) return HZ_ERR_ARG;
+      c->opt_dec_threads = (int)v;
+      return HZ_OK;
+    case HZ_OPT_AUTOTUNE:
+      if (v != 0 && v != 1) return HZ_ERR_ARG;
+      c->opt_autotune = (int)v;
+      return HZ_OK;
+    default:
+      return HZ_ERR_ARG;
+  }
+}
+
+int64_t hz_get_option(hz_ctx* c, int key) {
+  if (!c) return -1;
+  switch (key) {
+    case HZ_OPT_INDEX: return c->opt_index;
+    case HZ_OPT_PROFILE: return c->opt_profile;
+    case HZ_OPT_DECODE_LUT_BITS: return c->opt_lut_bits;
+    case HZ_OPT_DECODE_THREADS: return c->opt_dec_threads;
+    case HZ_OPT_AUTOTUNE: return c->opt_autotune;
+    default: return -1;
+  }
+}
+
+uint64_t hz_launch_count(hz_ctx* c) { return c ? c->launches : 0; }
+
+const char* hz_kernel_name(int32_t id) {
+  static const char* names[] = {"histogram", "build_codes", "encode", "decode_setup",
+                                "decode", "index_chase", "batch"};
+  if (id < 0 || id >= (int32_t)(sizeof(names) / sizeof(names[0]))) return "?";
+  return names[id];
+}
+
+int hz_profile_read(hz_ctx* c, int32_t* ids, float* ms, int max) {
+  if (!c) return 0;
+  DeviceGuard g(c->device);
+  int k = 0;
+  for (auto& r : c->prof) {
+    float t = 0.f;
+    cudaEventSynchronize(r.b);
+    cudaEventElapsedTime(&t, r.a, r.b);
+    if (k < max) {
+      if (ids) ids[k] = r.id;
+      if (ms) ms[k] = t;
+      ++k;
+    }
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  c->prof.clear();
+  return k;
+}
+
+hz_status hz_sync(hz_ctx* c, void* stream) {
+  if (!c) return HZ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return HZ_ERR_CUDA;
+  }
+  if (cudaMemcpy(c->h_err, c->d_state, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HZ_ERR_CUDA;
+  const uint32_t e = c->h_err[0];
+  if (e) {
+    if (cudaMemset(c->d_state, 0, 2 * sizeof(uint32_t)) != cudaSuccess) return HZ_ERR_CUDA;
+    return -(hz_status)e;
+  }
+  return HZ_OK;
+}
+
+// Enqueue histogram + code construction (Sec. 2) into the context state.
+static hz_status enqueue_codes(hz_ctx* c, const uint8_t* d_in, uint64_t n, const hz_codes* codes,
+                               uint32_t B, uint32_t nb, uint32_t flags, uint8_t* d_out,
+                               uint64_t out_cap, uint64_t* d_out_len, cudaStream_t s) {
+  // clear the ticket counters and the histogram (the status word is kept)
+  if (cudaMemsetAsync(&c->d_state->tile_counter, 0,
+                      offsetof(DevState, codes) - offsetof(DevState, tile_counter), s) !=
+      cudaSuccess)
+    return HZ_ERR_CUDA;
+  LenParam given;
+  memset(&given, 0, sizeof(given));
+  hz_status st = HZ_OK;
+  if (codes) {
+    memcpy(given.len, codes->len, 256);
+  } else if (n > 0) {
+    st = launch(c, K_HIST, s, [&] { return launch_histogram(d_in, n, c->d_state, c->num_sms, s); });
+    if (st != HZ_OK) return st;
+  }
+  return launch(c, K_BUILD, s, [&] {
+    return launch_build_codes(c->d_state, codes ? 0 : 1, given, n, B, nb, flags, d_out, out_cap,
+                              d_out_len, s);
+  });
+}
+
+// Host-side check of a caller's code table: Kraft's inequality and canonical values.
+static bool codes_valid(const hz_codes* codes) {
+  uint64_t lo = 0, hi = 0;
+  for (int s = 0; s < 256; ++s) {
+    const int l = codes->len[s];
+    if (!l) continue;
+    if (l > kMaxLen) return false;
+    const uint64_t add = l == 64 ? 1 : (1ull << (64 - l));
+    const uint64_t prev = lo;
+    lo += add;
+    if (lo < prev) hi += 1;
+  }
+  if (!(hi == 0 || (hi == 1 && lo == 0))) return false;
+  uint64_t code = 0;
+  int prev_len = 0;
+  bool firstc = true;
+  for (int l = 1; l <= kMaxLen; ++l)
+    for (int s = 0; s < 256; ++s) {
+      if (codes->len[s] != l) continue;
+      code = firstc ? 0 : (code + 1) << (l - prev_len);
+      firstc = false;
+      prev_len = l;
+      if (codes->code[s] != code) return false;
+    }
+  return true;
+}
+
+hz_status hz_build_codes(hz_ctx* c, const uint8_t* d_in, uint64_t n, hz_codes* codes_out,
+                         void* stream) {
+  if (!c || !codes_out || n > 0xFFFFFFFFull || (n && !d_in)) return HZ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  hz_status st = enqueue_codes(c, d_in, n, nullptr, 1, 0, 0, nullptr, 0, nullptr, s);
+  if (st != HZ_OK) return st;
+  if (cudaMemcpyAsync(c->h_codes->len, c->d_state->codes.len, 256, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->h_codes->code, c->d_state->codes.code, 256 * sizeof(uint64_t),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return HZ_ERR_CUDA;
+  st = hz_sync(c, stream);
+  if (st != HZ_OK) return st;
+  memcpy(codes_out, c->h_codes, sizeof(hz_codes));
+  return HZ_OK;
+}
+
+hz_status hz_compress(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32_t block_size,
+                      const hz_codes* codes, uint8_t* d_out, uint64_t out_cap,
+                      uint64_t* d_out_len, void* stream) {
+  if (!c || !d_out || !d_out_len || n > 0xFFFFFFFFull || (n && !d_in)) return HZ_ERR_ARG;
+  if (((uintptr_t)d_out & 3) || ((uintptr_t)d_out_len & 7)) return HZ_ERR_ARG;
+  if (block_size > kMaxBlock) return HZ_ERR_ARG;
+  if (codes && !codes_valid(codes)) return HZ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t B = block_size ? block_size : autotuned_block(c, n);
+  const uint64_t nb64 = (n + B - 1) / B;
+  const uint32_t nb = (uint32_t)nb64;
+  const uint32_t flags = c->opt_index ? kFlagIndex : 0;
+  const uint32_t ntiles = (uint32_t)((n + kEncTile - 1) / kEncTile);
+  if (ntiles > c->tiles_cap) {
+    uint64_t cap = c->tiles_cap ? c->tiles_cap : 1024;
+    while (cap < ntiles) cap *= 2;
+    cudaFree(c->d_tiles);
+    c->d_tiles = nullptr;
+    c->tiles_cap = 0;
+    if (cudaMalloc(&c->d_tiles, cap * sizeof(TileStatus)) != cudaSuccess ||
+        cudaMemsetAsync(c->d_tiles, 0, cap * sizeof(TileStatus), s) != cudaSuccess) {
+      cudaGetLastError();
+      return HZ_ERR_NOMEM;
+    }
+    c->tiles_cap = (uint32_t)cap;
+    c->epoch = 0;
+  }
+  // the look-back flags carry a 30-bit launch epoch, so they never need clearing
+  c->epoch += 1;
+  if (c->epoch >= (1u << 30)) {
+    if (cudaMemsetAsync(c->d_tiles, 0, (uint64_t)c->tiles_cap * sizeof(TileStatus), s) !=
+        cudaSuccess)
+      return HZ_ERR_CUDA;
+    c->epoch = 1;
+  }
+  hz_status st = enqueue_codes(c, d_in, n, codes, B, nb, flags, d_out, out_cap, d_out_len, s);
+  if (st != HZ_OK || n == 0) return st;
+  EncodeArgs a;
+  a.in = d_in;
+  a.n = n;
+  a.B = B;
+  a.nb = nb;
+  a.flags = flags;
+  a.out = d_out;
+  a.out_cap = out_cap;
+  a.out_len = d_out_len;
+  a.st = c->d_state;
+  a.tiles = c->d_tiles;
+  a.ntiles = ntiles;
+  a.epoch = c->epoch;
+  return launch(c, K_ENCODE, s, [&] { return launch_encode(a, c->num_sms, s); });
+}
+
+hz_status hz_decompress(hz_ctx* c, const uint8_t* d_in, uint64_t in_len, uint8_t* d_out,
+                        uint64_t out_cap, uint64_t* d_out_len, void* stream) {
+  if (!c || !d_in || !d_out_len || ((uintptr_t)d_in & 3) || ((uintptr_t)d_out_len & 7))
+    return HZ_ERR_ARG;
+  if (out_cap && !d_out) return HZ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  DecodeArgs a;
+  a.in = d_in;
+  a.in_len = in_len;
+  a.out = d_out;
+  a.out_cap = out_cap;
+  a.out_len = d_out_len;
+  a.st = c->d_state;
+  a.chase_index = c->d_chase;
+  a.chase_cap = c->chase_cap;
+  a.lut_bits = c->opt_lut_bits;
+  hz_status st = launch(c, K_DECODE_SETUP, s, [&] { return launch_decode_setup(a, c->d_dec, s); });
+  if (st != HZ_OK) return st;
+  return launch(c, K_DECODE, s, [&] {
+    return launch_decode_blocks(a, c->d_dec, c->opt_dec_threads, c->num_sms, s);
+  });
+}
+
+hz_status hz_compress_host(hz_ctx* c, const uint8_t* h_in, uint64_t n, uint32_t block_size,
+                           uint8_t* h_out, uint64_t out_cap, uint64_t* out_len, void* stream) {
+  if (!c || !h_out || !out_len || (n && !h_in) || n > 0xFFFFFFFFull) return HZ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t bound = hz_compress_bound(n, block_size ? block_size : 1);
+  const uint64_t dcap = out_cap < bound ? out_cap : bound;
+  hz_status st = grow((void**)&c->d_hin, &c->d_hin_cap, n ? n : 16);
+  if (st == HZ_OK) st = grow((void**)&c->d_hout, &c->d_hout_cap, dcap ? dcap : 16);
+  if (st != HZ_OK) return st;
+  if (n && cudaMemcpyAsync(c->d_hin, h_in, n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return HZ_ERR_CUDA;
+  st = hz_compress(c, c->d_hin, n, block_size, nullptr, c->d_hout, dcap, c->d_len, stream);
+  if (st != HZ_OK) return st;
+  if (cudaMemcpyAsync(c->h_len, c->d_len, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return HZ_ERR_CUDA;
+  st = hz_sync(c, stream);
+  *out_len = *c->h_len;
+  if (st != HZ_OK) return st;
+  if (*out_len > out_cap) return HZ_ERR_CAPACITY;
+  if (cudaMemcpyAsync(h_out, c->d_hout, *out_len, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return HZ_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;
+}
+
+hz_status hz_decompress_host(hz_ctx* c, const uint8_t* h_in, uint64_t in_len, uint8_t* h_out,
+                             uint64_t out_cap, uint64_t* out_len, void* stream) {
+  if (!c || !h_in || !out_len || (out_cap && !h_out)) return HZ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  hz_status st = grow((void**)&c->d_hin, &c->d_hin_cap, in_len ? in_len : 16);
+  if (st == HZ_OK) st = grow((void**)&c->d_hout, &c->d_hout_cap, out_cap ? out_cap : 16);
+  if (st != HZ_OK) return st;
+  if (cudaMemcpyAsync(c->d_hin, h_in, in_len, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return HZ_ERR_CUDA;
+  st = hz_decompress(c, c->d_hin, in_len, c->d_hout, out_cap, c->d_len, stream);
+  if (st != HZ_OK) return st;
+  if (cudaMemcpyAsync(c->h_len, c->d_len, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return HZ_ERR_CUDA;
+  // the decoded size is known from the header once setup has run; copy back
+  // only after the status is known
+  st = hz_sync(c, stream);
+  *out_len = *c->h_len;
+  if (st != HZ_OK) return st;
+  if (*out_len && cudaMemcpyAsync(h_out, c->d_hout, *out_len, cudaMemcpyDeviceToHost, s) !=
+                      cudaSuccess)
+    return HZ_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;
+}
+
+hz_status hz_submit(hz_ctx* c, const hz_request* reqs, uint32_t count, uint64_t* ticket_out) {
+  if (!c || !ticket_out || (count && !reqs)) return HZ_ERR_ARG;
+  DeviceGuard g(c->device);
+  return hz_batch_submit(c->batch, c, reqs, count, ticket_out);
+}
+
+hz_status hz_poll(hz_ctx* c, uint64_t ticket, int64_t timeout_ns, hz_status* per_req,
+                  uint64_t* out_lens) {
+  if (!c) return HZ_ERR_ARG;
+  DeviceGuard g(c->device);
+  return hz_batch_poll(c->batch, ticket, timeout_ns, per_req, out_lens);
+}
+
+}  // extern "C"
+
+hz::DevState* hz_ctx_state(hz_ctx* c) { return c->d_state; }
