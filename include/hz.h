@@ -157,6 +157,32 @@ hz_status hz_compress_host(hz_ctx* ctx, const uint8_t* h_in, uint64_t n, uint32_
 hz_status hz_decompress_host(hz_ctx* ctx, const uint8_t* h_in, uint64_t in_len, uint8_t* h_out,
                              uint64_t out_cap, uint64_t* out_len, void* stream);
 
+/*
+ * hz_compress_noalloc: hz_compress (code built from d_in, block-offset index
+ * written) for callers that must not allocate device memory -- for example
+ * code that runs under a framework's caching allocator or a fixed memory
+ * reservation that a cudaMalloc would bypass, or a latency-critical path that
+ * cannot afford cudaMalloc's implicit synchronisation.  The paper has no
+ * counterpart; it is an interface addition.
+ *
+ * It takes no context and allocates nothing: its scratch is one file-scope
+ * device array of about 1 MiB, which every GPU that loads the library holds
+ * until the process exits.  That array bounds the input: n <= 2^28 bytes
+ * (256 MiB); larger n returns HZ_ERR_ARG at once.  The caller passes inputs
+ * and outputs as for hz_compress, plus d_status, a device int32 that receives
+ * the call's device-side status (0 or a negative hz_status, e.g.
+ * HZ_ERR_CAPACITY with *d_out_len = the size needed) once the work has run.
+ * The first call on a device looks up the array's device address and clears
+ * it, synchronously, with that device current; make that first call before
+ * any stream capture.  Every call shares the one array and clears what must
+ * start at zero, so calls that overlap on the GPU (different streams or host
+ * threads without ordering) race; order them.  Asynchronous on `stream`
+ * otherwise.  HZ_ERR_CUDA if a launch or the set-up fails.
+ */
+hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32_t block_size,
+                              uint8_t* d_out, uint64_t out_cap, uint64_t* d_out_len,
+                              int32_t* d_status, void* stream);
+
 /* ------------------------------------------------------------- options */
 #define HZ_OPT_INDEX 1        /* 1 (default): write the block-offset index */
 #define HZ_OPT_PROFILE 2      /* 1: time every kernel launch with CUDA events */

@@ -30,7 +30,7 @@ HZ_OP_COMPRESS, HZ_OP_DECOMPRESS = 0, 1
 EXPORTS = ("hz_create", "hz_destroy", "hz_compress_bound", "hz_build_codes", "hz_compress",
            "hz_decompress", "hz_sync", "hz_compress_host", "hz_decompress_host",
            "hz_set_option", "hz_get_option", "hz_launch_count", "hz_profile_read",
-           "hz_kernel_name", "hz_submit", "hz_poll")
+           "hz_kernel_name", "hz_submit", "hz_poll", "hz_compress_noalloc")
 
 
 class HzError(RuntimeError):
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hz_kernel_name": (ctypes.c_char_p, [i32]),
         "hz_submit": (i32, [vp, ctypes.POINTER(HzRequest), u32, ctypes.POINTER(u64)]),
         "hz_poll": (i32, [vp, u64, i64, vp, vp]),
+        "hz_compress_noalloc": (i32, [vp, u64, u32, vp, u64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -195,6 +196,14 @@ def hz_decompress(ctx: Context, d_in, in_len: int, d_out, out_cap: int, d_out_le
                   stream=None) -> int:
     return _check(ctx._lib.hz_decompress(ctx.handle, _ptr(d_in), in_len, _ptr(d_out), out_cap,
                                          _ptr(d_out_len), _stream(stream)), "hz_decompress")
+
+
+def hz_compress_noalloc(d_in, n: int, block_size: int, d_out, out_cap: int, d_out_len,
+                        d_status, stream=None) -> int:
+    """No context, no device allocation (scratch is a fixed device array; n <= 2^28)."""
+    return _check(load_library().hz_compress_noalloc(_ptr(d_in), n, block_size, _ptr(d_out),
+                                                     out_cap, _ptr(d_out_len), _ptr(d_status),
+                                                     _stream(stream)), "hz_compress_noalloc")
 
 
 def hz_sync(ctx: Context, stream=None) -> int:
