@@ -33,6 +33,9 @@ WORKLOADS = {
     "mixed-1GiB": dict(n=GiB, segment=64 * MiB, block=65536,
                        desc="1 GiB uint8 in 64 MiB segments cycling Zipf(1.1) / geometric(0.3) "
                             "clipped to 255 / uniform-256 / uniform-16, 64 KiB blocks"),
+    "mixed-256MiB": dict(n=256 * MiB, segment=64 * MiB, block=65536,
+                         desc="256 MiB: one 64 MiB segment of each kind of the 1 GiB mix, "
+                              "64 KiB blocks (profiling case)"),
     "zipf-1MiB": dict(n=MiB, block=4096, desc="1 MiB i.i.d. Zipf(1.1) bytes, 4 KiB blocks"),
     "field-256MiB": dict(n=1 << 28, block=16384,
                          desc="2^28 int8 residuals of a smooth 512x512x1024 Gaussian field, "
@@ -55,7 +58,7 @@ def load_peaks():
 def make_input(name, device):
     import datagen
     w = WORKLOADS[name]
-    if name == "mixed-1GiB":
+    if name.startswith("mixed"):
         return datagen.mixed_buffer(n=w["n"], segment=w["segment"], seed=2, device=device)
     if name == "zipf-1MiB":
         return datagen.zipf_buffer(w["n"], s=1.1, seed=0, device=device)
@@ -165,7 +168,7 @@ def oracle_sample(name: str, sample_bytes: int):
     import datagen
     import torch
     w = WORKLOADS[name]
-    if name == "mixed-1GiB":
+    if name.startswith("mixed"):
         per = sample_bytes // 4
         parts = [datagen.sample_iid(datagen.segment_pmf(k), per, (2 << 16) + j, "cpu")
                  for j, k in enumerate(datagen.SEGMENT_KINDS)]
@@ -283,11 +286,13 @@ def run_gpu(args, world, rank, local, pg):
         d = per_kernel.setdefault(name, [0.0, 0])
         d[0] += t
         d[1] += 1
-    enc_ms = sum(per_kernel.get(k, [0, 0])[0] for k in ("histogram", "build_codes", "encode")) \
-        / args.steps
+    enc_kernels = ("histogram", "build_codes", "encode_summary", "encode_scan", "encode_pack")
+    enc_ms = sum(per_kernel.get(k, [0, 0])[0] for k in enc_kernels) / args.steps
     dec_ms = sum(per_kernel.get(k, [0, 0])[0] for k in ("decode_setup", "decode")) / args.steps
     # algorithmic bytes per launch of each kernel
-    algo = {"histogram": n, "encode": n + stream_len, "decode": stream_len + n,
+    ntiles = (n + 8191) // 8192
+    algo = {"histogram": n, "encode_summary": n, "encode_scan": 32 * ntiles,
+            "encode_pack": n + stream_len, "decode": stream_len + n,
             "build_codes": 1024, "decode_setup": 8192}
     dom = max(per_kernel, key=lambda k: per_kernel[k][0])
     dom_avg_ms = per_kernel[dom][0] / per_kernel[dom][1]

@@ -27,7 +27,6 @@ struct hz_ctx {
   DecTables* d_dec = nullptr;
   TileStatus* d_tiles = nullptr;
   uint32_t tiles_cap = 0;
-  uint32_t epoch = 0;
   uint32_t* d_chase = nullptr;
   uint32_t chase_cap = 0;
   uint32_t* h_err = nullptr;  // pinned readback of the status words
@@ -42,7 +41,7 @@ struct hz_ctx {
   // options
   int opt_index = 1;
   int opt_profile = 0;
-  int opt_lut_bits = 11;
+  int opt_lut_bits = 12;
   int opt_dec_threads = 256;
   int opt_autotune = 1;
   uint64_t launches = 0;
@@ -228,8 +227,9 @@ int64_t hz_get_option(hz_ctx* c, int key) {
 uint64_t hz_launch_count(hz_ctx* c) { return c ? c->launches : 0; }
 
 const char* hz_kernel_name(int32_t id) {
-  static const char* names[] = {"histogram", "build_codes", "encode", "decode_setup",
-                                "decode", "index_chase", "batch"};
+  static const char* names[] = {"histogram",   "build_codes",  "encode_summary", "encode_scan",
+                                "encode_pack", "decode_setup", "decode",         "decode_generic",
+                                "batch"};
   if (id < 0 || id >= (int32_t)(sizeof(names) / sizeof(names[0]))) return "?";
   return names[id];
 }
@@ -361,21 +361,11 @@ hz_status hz_compress(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32_t block
     cudaFree(c->d_tiles);
     c->d_tiles = nullptr;
     c->tiles_cap = 0;
-    if (cudaMalloc(&c->d_tiles, cap * sizeof(TileStatus)) != cudaSuccess ||
-        cudaMemsetAsync(c->d_tiles, 0, cap * sizeof(TileStatus), s) != cudaSuccess) {
+    if (cudaMalloc(&c->d_tiles, cap * sizeof(TileStatus)) != cudaSuccess) {
       cudaGetLastError();
       return HZ_ERR_NOMEM;
     }
     c->tiles_cap = (uint32_t)cap;
-    c->epoch = 0;
-  }
-  // the look-back flags carry a 30-bit launch epoch, so they never need clearing
-  c->epoch += 1;
-  if (c->epoch >= (1u << 30)) {
-    if (cudaMemsetAsync(c->d_tiles, 0, (uint64_t)c->tiles_cap * sizeof(TileStatus), s) !=
-        cudaSuccess)
-      return HZ_ERR_CUDA;
-    c->epoch = 1;
   }
   hz_status st = enqueue_codes(c, d_in, n, codes, B, nb, flags, d_out, out_cap, d_out_len, s);
   if (st != HZ_OK || n == 0) return st;
@@ -391,8 +381,11 @@ hz_status hz_compress(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32_t block
   a.st = c->d_state;
   a.tiles = c->d_tiles;
   a.ntiles = ntiles;
-  a.epoch = c->epoch;
-  return launch(c, K_ENCODE, s, [&] { return launch_encode(a, c->num_sms, s); });
+  a.fdB = make_fastdiv(B);
+  st = launch(c, K_ENC_SUMMARY, s, [&] { return launch_encode_summary(a, c->num_sms, s); });
+  if (st == HZ_OK) st = launch(c, K_ENC_SCAN, s, [&] { return launch_encode_scan(a, s); });
+  if (st == HZ_OK) st = launch(c, K_ENC_PACK, s, [&] { return launch_encode_pack(a, c->num_sms, s); });
+  return st;
 }
 
 hz_status hz_decompress(hz_ctx* c, const uint8_t* d_in, uint64_t in_len, uint8_t* d_out,
@@ -414,9 +407,12 @@ hz_status hz_decompress(hz_ctx* c, const uint8_t* d_in, uint64_t in_len, uint8_t
   a.lut_bits = c->opt_lut_bits;
   hz_status st = launch(c, K_DECODE_SETUP, s, [&] { return launch_decode_setup(a, c->d_dec, s); });
   if (st != HZ_OK) return st;
-  return launch(c, K_DECODE, s, [&] {
+  st = launch(c, K_DECODE, s, [&] {
     return launch_decode_blocks(a, c->d_dec, c->opt_dec_threads, c->num_sms, s);
   });
+  if (st != HZ_OK) return st;
+  return launch(c, K_DECODE_GENERIC, s,
+                [&] { return launch_decode_generic(a, c->d_dec, c->num_sms, s); });
 }
 
 hz_status hz_compress_host(hz_ctx* c, const uint8_t* h_in, uint64_t n, uint32_t block_size,

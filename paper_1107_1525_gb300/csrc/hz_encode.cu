@@ -1,29 +1,29 @@
 // hz_encode.cu -- block encoder (Sec. 2.1 and Figs. 3-4 of Cloud et al.).
 //
 // Every block of B symbols becomes a record [u32 bits_k][payload words],
-// where bits_k is the sum of the block's code lengths (the paper's "additional
-// pass ... summing the lengths of the code representation") and the payload
-// is padded to a 32-bit boundary.  Records are laid out back to back, so the
-// position of every record depends on the sizes of all earlier ones.
+// where bits_k is the sum of the block's code lengths (the paper's
+// "additional pass ... summing the lengths of the code representation") and
+// the payload is padded to a 32-bit boundary.  Records are laid out back to
+// back, so a record's position depends on the sizes of all earlier records.
 //
-// One kernel does the whole encode in a single read of the input:
-//   * persistent CTAs take 8192-symbol tiles from a ticket counter, so a tile
-//     only ever waits on tiles that are already running;
-//   * each thread holds 32 consecutive symbols in registers and summarises
-//     them as a segment (see Summary below) -- this is the length-sum pass,
-//     fused with the load;
-//   * a CTA scan combines the thread summaries, and a decoupled look-back over
-//     earlier tiles (32 predecessors per warp step) yields the tile's exclusive
-//     prefix: the word position of the open record and the bits already in it;
-//   * each thread then packs its codes, MSB first, into 32-bit words with a
-//     64-bit shift accumulator, staging the tile's words in shared memory
-//     (shared-memory atomicOr only for words split between two threads), and
-//     the CTA writes the staged words out with coalesced stores;
-//   * a word split between two tiles is written by the later tile, which
-//     re-derives the earlier tile's last (< 32) bits from the input; the
-//     delimiter of a record that spans tiles is written by the tile holding
-//     the record's last symbol.  No word is ever written twice, and the output
-//     buffer needs no clearing.
+// Three launches, no inter-CTA waiting:
+//   1. encode_summary_kernel -- the length-summing pass: every 8192-symbol
+//      tile is reduced to a Summary (below) of its code lengths and record
+//      starts;
+//   2. encode_scan_kernel -- one CTA scans the tile summaries into each
+//      tile's start state (word position of the open record, bits already in
+//      it), fixes the stream size and checks it against the output capacity;
+//   3. encode_pack_kernel -- every tile is packed independently from its
+//      start state: each thread packs 32 consecutive symbols MSB-first with a
+//      64-bit shift accumulator (two codes per step when codes have at most
+//      16 bits), the tile's words are staged in shared memory (atomicOr only
+//      for a word split between two threads) and written out with 16-byte
+//      stores.  Tiles run last-to-first so the first ones packed are those the
+//      length-summing pass read last, still in L2.
+// A word split between two tiles is written by the later tile, which
+// re-derives the earlier tile's last (< 32) bits from the input; the
+// delimiter of a record is written by the tile holding the record's last
+// symbol.  No word is written twice and the output needs no clearing.
 #include "hz_internal.cuh"
 
 namespace hz {
@@ -75,15 +75,6 @@ __device__ __forceinline__ ScanState apply(const ScanState& s, const Summary& x)
   return r;
 }
 
-__device__ __forceinline__ Summary shfl_summary(const Summary& v, int src) {
-  Summary r;
-  r.has = __shfl_sync(0xFFFFFFFFu, v.has, src);
-  r.head = __shfl_sync(0xFFFFFFFFu, v.head, src);
-  r.omega = __shfl_sync(0xFFFFFFFFu, v.omega, src);
-  r.tail = __shfl_sync(0xFFFFFFFFu, v.tail, src);
-  return r;
-}
-
 __device__ __forceinline__ Summary shfl_up_summary(const Summary& v, int d) {
   Summary r;
   r.has = __shfl_up_sync(0xFFFFFFFFu, v.has, d);
@@ -93,26 +84,548 @@ __device__ __forceinline__ Summary shfl_up_summary(const Summary& v, int d) {
   return r;
 }
 
-struct EncShared {
-  uint32_t entry[256];       // code << 6 | len   (codes of up to 26 bits)
-  uint32_t len[256];
-  uint32_t code_lo[256];
-  uint32_t code_hi[256];
-  Summary warp_sum[kEncThreads / 32];
-  uint32_t stage[kEncStageWords];
-  ScanState excl;            // tile exclusive prefix
-  Summary agg;               // tile aggregate
-  uint32_t tile;
-  uint32_t prev_bits;        // bits of the previous tile in this tile's first word
-  uint32_t abort;
-};
+__device__ __forceinline__ Summary load_summary(const TileStatus& t) {
+  return Summary{t.has_head >> 31, t.has_head & 0x7FFFFFFFu, t.omega, t.tail};
+}
+
+__device__ __forceinline__ void store_summary(TileStatus& t, const Summary& s) {
+  t.has_head = (s.has << 31) | s.head;
+  t.omega = s.omega;
+  t.tail = s.tail;
+}
+
+// a virtual empty record before the first one: its "next record" is word 0
+__device__ __forceinline__ ScanState init_state() { return ScanState{~0ull, 0u}; }
 
 __device__ __forceinline__ uint32_t sym_of(const uint32_t (&x)[kEncSymPerThread / 4], int i) {
   return (x[i >> 2] >> (8 * (i & 3))) & 0xFFu;
 }
 
-// Writer for one thread's words: words inside the current staging window go
-// to shared memory, others are dropped (a later window pass writes them).
+// The thread's 32 consecutive symbols (fewer at the end of the input).
+__device__ __forceinline__ void load_symbols(const uint8_t* src, int cnt,
+                                             uint32_t (&x)[kEncSymPerThread / 4]) {
+  if (cnt == kEncSymPerThread && (((uintptr_t)src) & 15) == 0) {
+    uint4 v0 = __ldg(reinterpret_cast<const uint4*>(src));
+    uint4 v1 = __ldg(reinterpret_cast<const uint4*>(src) + 1);
+    x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+    x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+  } else {
+    // static indices only, so that x stays in registers
+#pragma unroll
+    for (int w = 0; w < kEncSymPerThread / 4; ++w) x[w] = 0;
+#pragma unroll
+    for (int i = 0; i < kEncSymPerThread; ++i)
+      if (i < cnt) x[i >> 2] |= (uint32_t)src[i] << (8 * (i & 3));
+  }
+}
+
+struct TileGeom {
+  uint32_t lo, hi, g0;  // n < 2^32, so every symbol index fits 32 bits
+  int my_cnt;
+  bool starts_record, ends_record, interior_start;
+};
+
+__device__ __forceinline__ TileGeom tile_geom(uint32_t tile, uint32_t n, const FastDiv& fdB) {
+  TileGeom g;
+  g.lo = tile * (uint32_t)kEncTile;
+  g.hi = n - g.lo > (uint32_t)kEncTile ? g.lo + (uint32_t)kEncTile : n;
+  g.g0 = g.lo + threadIdx.x * (uint32_t)kEncSymPerThread;
+  g.my_cnt = g.g0 >= g.hi ? 0 : (int)min(g.hi - g.g0, (uint32_t)kEncSymPerThread);
+  const uint32_t r_lo = fast_mod(g.lo, fdB);
+  g.starts_record = r_lo == 0;
+  g.ends_record = fast_mod(g.hi, fdB) == 0 || g.hi == n;
+  // first record start after lo: lo + (B - r_lo)
+  g.interior_start = (uint64_t)g.lo + (fdB.d - r_lo) < g.hi;
+  return g;
+}
+
+// Segment summary of one thread's symbols; lens() maps a symbol to its length.
+template <class LenF>
+__device__ __forceinline__ Summary thread_summary(const uint32_t (&x)[kEncSymPerThread / 4],
+                                                  int my_cnt, uint32_t g0, const FastDiv& fdB,
+                                                  LenF lens, bool& bad) {
+  const uint32_t r0 = fast_mod(g0, fdB);
+  uint32_t next_start = r0 == 0 ? 0u : fdB.d - r0;
+  Summary s{0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < kEncSymPerThread; ++i) {
+    if (i < my_cnt) {
+      const uint32_t l = lens(sym_of(x, i));
+      bad |= l == 0;
+      if ((uint32_t)i == next_start) {
+        if (s.has) s.omega += 1 + ceil32(s.tail);
+        s.has = 1;
+        s.tail = 0;
+        next_start += fdB.d;
+      }
+      if (s.has) s.tail += l;
+      else s.head += l;
+    }
+  }
+  return s;
+}
+
+// =================================================================== pass 1
+__global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs a) {
+  __shared__ uint8_t s_len[256];  // 64 words: random lookups conflict at most 2-way
+  __shared__ uint32_t s_wsum[kEncThreads / 32];
+  __shared__ Summary s_warp[kEncThreads / 32];
+  const CodeTable* ct = &a.st->codes;
+  if (ct->maxlen > (uint32_t)kMaxLen) return;  // code construction failed; already reported
+  for (int s = threadIdx.x; s < 256; s += kEncThreads) s_len[s] = ct->len[s];
+  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  bool bad = false;
+  for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const TileGeom g = tile_geom(tile, (uint32_t)a.n, a.fdB);
+    uint32_t x[kEncSymPerThread / 4];
+    load_symbols(a.in + g.g0, g.my_cnt, x);
+    if (!g.interior_start) {
+      // the tile lies inside one record (which may start at its first symbol)
+      uint32_t bits = 0, minl = 64;
+      if (g.my_cnt == kEncSymPerThread) {
+#pragma unroll
+        for (int i = 0; i < kEncSymPerThread; ++i) {
+          const uint32_t l = s_len[sym_of(x, i)];
+          minl = min(minl, l);
+          bits += l;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < kEncSymPerThread; ++i) {
+          if (i < g.my_cnt) {
+            const uint32_t l = s_len[sym_of(x, i)];
+            minl = min(minl, l);
+            bits += l;
+          }
+        }
+      }
+      bad |= minl == 0;
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, d);
+      if (lane == 0) s_wsum[warp] = bits;
+      __syncthreads();
+      if (tid == 0) {
+        uint32_t total = 0;
+        for (int w = 0; w < kEncThreads / 32; ++w) total += s_wsum[w];
+        store_summary(a.tiles[tile], g.starts_record ? Summary{1, 0, 0, total}
+                                                     : Summary{0, total, 0, 0});
+      }
+    } else {
+      Summary s = thread_summary(x, g.my_cnt, g.g0, a.fdB, [&](uint32_t v) { return s_len[v]; },
+                                 bad);
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        Summary o = shfl_up_summary(s, d);
+        if (lane >= d) s = combine(o, s);
+      }
+      if (lane == 31) s_warp[warp] = s;
+      __syncthreads();
+      if (tid == 0) {
+        Summary t{0, 0, 0, 0};
+        for (int w = 0; w < kEncThreads / 32; ++w) t = combine(t, s_warp[w]);
+        store_summary(a.tiles[tile], t);
+      }
+    }
+    __syncthreads();
+  }
+  if (bad) set_error(a.st, HZ_ERR_ARG, 0x200);  // a byte without a code (caller's code table)
+}
+
+// =================================================================== pass 2
+// Each CTA scans kScanTilesPerCta consecutive tile summaries (4 per thread);
+// CTAs take their index from a ticket and find their exclusive prefix by a
+// look-back over the aggregates of earlier CTAs (at most 128 of them).
+constexpr int kScanThreads = 1024;
+constexpr int kScanPerThread = kScanTilesPerCta / kScanThreads;
+
+__global__ void __launch_bounds__(kScanThreads) encode_scan_kernel(EncodeArgs a) {
+  __shared__ Summary s_warp[kScanThreads / 32];
+  __shared__ uint32_t s_cta;
+  __shared__ ScanState s_excl;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  DevState* st = a.st;
+  if (tid == 0) {
+    s_cta = atomicAdd(&st->tile_counter, 1u);  // ticket order: predecessors are running
+    s_abort = 0;
+  }
+  __syncthreads();
+  const uint32_t cta = s_cta;
+  const uint32_t nt = a.ntiles;
+  const uint32_t t0 = cta * kScanTilesPerCta + tid * kScanPerThread;
+  Summary mine[kScanPerThread];
+  Summary agg{0, 0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    mine[k] = t0 + k < nt ? load_summary(a.tiles[t0 + k]) : Summary{0, 0, 0, 0};
+    agg = combine(agg, mine[k]);
+  }
+  Summary inc = agg;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    Summary o = shfl_up_summary(inc, d);
+    if (lane >= d) inc = combine(o, inc);
+  }
+  Summary ex = shfl_up_summary(inc, 1);
+  if (lane == 0) ex = Summary{0, 0, 0, 0};
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  Summary wpre{0, 0, 0, 0}, cta_agg{0, 0, 0, 0};
+  for (int w = 0; w < kScanThreads / 32; ++w) {
+    if (w < warp) wpre = combine(wpre, s_warp[w]);
+    cta_agg = combine(cta_agg, s_warp[w]);
+  }
+  ex = combine(wpre, ex);
+
+  if (warp == 0) {
+    TileStatus* aux = st->scan_aux;
+    if (cta == 0) {
+      if (lane == 0) {
+        const ScanState incl = apply(init_state(), cta_agg);
+        aux[0].pre_O = incl.O;
+        aux[0].pre_b = incl.b;
+        st_release(&st->scan_flags[0], 2u);
+        s_excl = init_state();
+      }
+    } else {
+      if (lane == 0) {
+        store_summary(aux[cta], cta_agg);
+        st_release(&st->scan_flags[cta], 1u);
+      }
+      Summary acc{0, 0, 0, 0};
+      int j = (int)cta - 1;
+      bool timed_out = false;
+      ScanState result = init_state();
+      for (;;) {
+        const int idx = j - lane;
+        uint32_t state = 2;  // index -1 stands for the virtual start state
+        Summary ag{0, 0, 0, 0};
+        ScanState pre = init_state();
+        if (idx >= 0) {
+          uint32_t f = ld_acquire(&st->scan_flags[idx]);
+          uint32_t spins = 0;
+          while (f == 0) {
+            if (++spins > kSpinLimit) {
+              timed_out = true;
+              break;
+            }
+            __nanosleep(64);
+            f = ld_acquire(&st->scan_flags[idx]);
+          }
+          state = timed_out ? 2u : f;
+          if (state == 1) ag = load_summary(aux[idx]);
+          else if (!timed_out) pre = ScanState{aux[idx].pre_O, aux[idx].pre_b};
+        }
+        const uint32_t pmask = __ballot_sync(0xFFFFFFFFu, state == 2);
+        const int stop = pmask ? __ffs(pmask) - 1 : 32;
+        Summary c{0, 0, 0, 0};
+        for (int l = stop - 1; l >= 0; --l) {
+          Summary v;
+          v.has = __shfl_sync(0xFFFFFFFFu, ag.has, l);
+          v.head = __shfl_sync(0xFFFFFFFFu, ag.head, l);
+          v.omega = __shfl_sync(0xFFFFFFFFu, ag.omega, l);
+          v.tail = __shfl_sync(0xFFFFFFFFu, ag.tail, l);
+          c = combine(c, v);
+        }
+        acc = combine(c, acc);
+        if (stop < 32) {
+          ScanState p;
+          p.O = __shfl_sync(0xFFFFFFFFu, pre.O, stop);
+          p.b = __shfl_sync(0xFFFFFFFFu, pre.b, stop);
+          result = apply(p, acc);
+          break;
+        }
+        j -= 32;
+      }
+      const bool any_timeout = __any_sync(0xFFFFFFFFu, timed_out);
+      if (lane == 0) {
+        if (any_timeout) {
+          set_error(st, HZ_ERR_TIMEOUT, 0x205);
+          s_abort = 1;
+        }
+        const ScanState incl = apply(result, cta_agg);
+        aux[cta].pre_O = incl.O;
+        aux[cta].pre_b = incl.b;
+        st_release(&st->scan_flags[cta], 2u);  // published even after a time-out
+        s_excl = result;
+      }
+    }
+  }
+  __syncthreads();
+  ScanState s = apply(s_excl, ex);
+#pragma unroll
+  for (int k = 0; k < kScanPerThread; ++k) {
+    if (t0 + k < nt) {
+      a.tiles[t0 + k].pre_O = s.O;
+      a.tiles[t0 + k].pre_b = s.b;
+      s = apply(s, mine[k]);
+      if (t0 + k == nt - 1) {
+        // the thread holding the last tile knows the whole stream
+        const uint64_t rec_base = kHeaderBytes + ((a.flags & kFlagIndex) ? 4ull * a.nb : 0ull);
+        const uint64_t words = s.O + 1 + ceil32(s.b);
+        const uint64_t size = rec_base + 4 * words;
+        *a.out_len = size;
+        bool ok = st->error == 0 && !s_abort;
+        if (size > a.out_cap || words > 0xFFFFFFFFull) {
+          set_error(st, HZ_ERR_CAPACITY, 0x203);
+          ok = false;
+        }
+        st->enc_ok = ok ? 1u : 0u;
+      }
+    }
+  }
+}
+
+// =================================================================== pass 3
+struct PackShared {
+  EncodeArgs a;         // the launch arguments, read by the per-tile functions
+  uint32_t entry[256];  // code << 6 | len, valid for codes of up to 26 bits
+  uint32_t len[256];
+  uint32_t code_lo[256];
+  uint32_t code_hi[256];
+  uint32_t wsum[kEncThreads / 32];
+  Summary warp_sum[kEncThreads / 32];
+  uint32_t prev_bits;
+  __align__(16) uint32_t stage[kEncStageWords + 4];
+};
+
+template <bool kLong>
+__device__ __forceinline__ void lookup(const PackShared& sh, uint32_t sym, uint32_t& l,
+                                       uint64_t& c) {
+  if (!kLong) {
+    const uint32_t e = sh.entry[sym];
+    l = e & 63u;
+    c = e >> 6;
+  } else {
+    l = sh.len[sym];
+    c = ((uint64_t)sh.code_hi[sym] << 32) | sh.code_lo[sym];
+  }
+}
+
+// The r (< 32) payload bits just before input position `pos` (all inside the
+// record that continues at `pos`), right-aligned.
+template <bool kLong>
+__device__ uint32_t bits_before(const PackShared& sh, const uint8_t* in, uint32_t pos,
+                                uint32_t r) {
+  uint64_t v = 0;
+  uint32_t got = 0;
+  int64_t j = (int64_t)pos - 1;
+  while (got < r && j >= 0) {
+    uint32_t l;
+    uint64_t c;
+    lookup<kLong>(sh, in[j], l, c);
+    if (got < 64) v |= c << got;
+    got += l;
+    --j;
+  }
+  return (uint32_t)(v & ((1u << r) - 1u));
+}
+
+// Pack one thread's 32 cached entries (code << 6 | len) MSB-first into
+// st[wrel...], starting `nacc` bits into word wrel.  A word that may hold an
+// earlier thread's bits (the first one, when nacc != 0) or a later thread's
+// (the last, partial one) is combined with atomicOr.
+template <bool kPair>
+__device__ __forceinline__ void pack_entries(const uint32_t (&e)[kEncSymPerThread], uint32_t* st,
+                                             uint32_t wrel, uint32_t nacc) {
+  bool first_shared = nacc != 0;
+  uint64_t acc = 0;
+  auto push = [&](uint32_t c, uint32_t l) {
+    acc = (acc << l) | c;
+    nacc += l;
+    if (nacc >= 32) {
+      nacc -= 32;
+      const uint32_t v = (uint32_t)(acc >> nacc);
+      if (first_shared) atomicOr(st + wrel, v);
+      else st[wrel] = v;
+      first_shared = false;
+      ++wrel;
+    }
+  };
+  if (kPair) {
+#pragma unroll
+    for (int j = 0; j < kEncSymPerThread / 2; ++j) {
+      const uint32_t ea = e[2 * j], eb = e[2 * j + 1];
+      const uint32_t lb = eb & 63u;
+      push(((ea >> 6) << lb) | (eb >> 6), (ea & 63u) + lb);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kEncSymPerThread; ++i) push(e[i] >> 6, e[i] & 63u);
+  }
+  if (nacc) atomicOr(st + wrel, (uint32_t)(acc << (32 - nacc)));
+}
+
+// Write stage[off .. end) to gbase[off .. end) with 16-byte stores where a
+// whole aligned chunk is inside the range, skipping index skip_i.
+__device__ __forceinline__ void copy_out(const uint32_t* stage, uint32_t* gbase, uint32_t off,
+                                         uint32_t end, uint32_t skip_i) {
+  const uint32_t nchunks = (end + 3) >> 2;
+  for (uint32_t c = threadIdx.x; c < nchunks; c += kEncThreads) {
+    const uint32_t i0 = c << 2;
+    if (i0 >= off && i0 + 4 <= end && (skip_i < i0 || skip_i >= i0 + 4)) {
+      *reinterpret_cast<uint4*>(gbase + i0) = *reinterpret_cast<const uint4*>(stage + i0);
+    } else {
+#pragma unroll
+      for (uint32_t k = 0; k < 4; ++k) {
+        const uint32_t i = i0 + k;
+        if (i >= off && i < end && i != skip_i) gbase[i] = stage[i];
+      }
+    }
+  }
+}
+
+// Single-record path: the tile lies inside one record (which may start at its
+// first symbol) and codes have at most 26 bits; thread positions come from a
+// plain scan of bit counts.
+template <bool kPair>
+__device__ __noinline__ void pack_tile_single(PackShared& sh, uint32_t tile, const TileGeom g,
+                                                 uint32_t* rec_words) {
+  const EncodeArgs& a = sh.a;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const ScanState S{a.tiles[tile].pre_O, a.tiles[tile].pre_b};
+  const uint64_t O1 = g.starts_record ? S.O + 1 + ceil32(S.b) : S.O;
+  const uint32_t b0 = g.starts_record ? 0u : S.b;
+
+  uint32_t x[kEncSymPerThread / 4];
+  load_symbols(a.in + g.g0, g.my_cnt, x);
+  uint32_t e[kEncSymPerThread];
+  uint32_t bits = 0;
+#pragma unroll
+  for (int i = 0; i < kEncSymPerThread; ++i) {
+    e[i] = i < g.my_cnt ? sh.entry[sym_of(x, i)] : 0u;
+    bits += e[i] & 63u;
+  }
+  uint32_t inc = bits;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  if (lane == 31) sh.wsum[warp] = inc;
+  __syncthreads();
+  uint32_t wpre = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < kEncThreads / 32; ++w) {
+    const uint32_t v = sh.wsum[w];
+    wpre += w < warp ? v : 0u;
+    total += v;
+  }
+  const uint32_t ex = wpre + inc - bits;
+  const uint32_t bend = b0 + total;
+  const uint64_t W0 = O1 + 1 + (b0 >> 5);
+  const uint32_t nwords = ((bend - 1) >> 5) - (b0 >> 5) + 1;
+  const uint32_t off = (uint32_t)((((uintptr_t)rec_words) >> 2) + W0) & 3u;
+  if (total == 0 || off + nwords > (uint32_t)kEncStageWords + 4) {
+    if (tid == 0) set_error(a.st, HZ_ERR_ARG, 0x206);
+    return;  // uniform
+  }
+  const uint32_t r_prev = b0 & 31u;
+  for (uint32_t i = tid; i < off + nwords; i += kEncThreads) sh.stage[i] = 0;
+  if (tid == 0 && r_prev) sh.prev_bits = bits_before<false>(sh, a.in, g.lo, r_prev);
+  __syncthreads();
+  if (tid == 0 && r_prev) sh.stage[off] = sh.prev_bits << (32 - r_prev);
+  __syncthreads();
+  if (bits) {
+    const uint32_t p = b0 + ex;
+    pack_entries<kPair>(e, sh.stage + off, (p >> 5) - (b0 >> 5), p & 31u);
+  }
+  __syncthreads();
+  // the last word belongs to the next tile when the record goes on mid-word
+  const bool skip_last = !g.ends_record && (bend & 31u) != 0;
+  copy_out(sh.stage, rec_words + (W0 - off), off, off + nwords - (skip_last ? 1u : 0u),
+           0xFFFFFFFFu);
+  if (tid == 0) {
+    if (g.ends_record) rec_words[O1] = bend;  // this tile holds the record's last symbol
+    if (g.starts_record && (a.flags & kFlagIndex))
+      reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[fast_div(g.lo, a.fdB)] = (uint32_t)O1;
+  }
+}
+
+// Chunked path: B is a multiple of 32, so records start and end only at the
+// boundaries of the threads' 32-symbol chunks, and codes have at most 26
+// bits.  Each chunk lies inside one record; a thread's start state comes from
+// a CTA scan of chunk summaries.
+template <bool kPair>
+__device__ __noinline__ void pack_tile_chunked(PackShared& sh, uint32_t tile, const TileGeom g,
+                                                  uint32_t* rec_words) {
+  const EncodeArgs& a = sh.a;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const ScanState S_s{a.tiles[tile].pre_O, a.tiles[tile].pre_b};
+
+  uint32_t x[kEncSymPerThread / 4];
+  load_symbols(a.in + g.g0, g.my_cnt, x);
+  uint32_t e[kEncSymPerThread];
+  uint32_t bits = 0;
+#pragma unroll
+  for (int i = 0; i < kEncSymPerThread; ++i) {
+    e[i] = i < g.my_cnt ? sh.entry[sym_of(x, i)] : 0u;
+    bits += e[i] & 63u;
+  }
+  const bool starts = g.my_cnt > 0 && fast_mod(g.g0, a.fdB) == 0;
+  const uint32_t gend = g.g0 + (uint32_t)g.my_cnt;
+  const bool ends = g.my_cnt > 0 && (fast_mod(gend, a.fdB) == 0 || gend == (uint32_t)a.n);
+  const Summary mine = starts ? Summary{1, 0, 0, bits} : Summary{0, bits, 0, 0};
+  Summary inc = mine;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    Summary o = shfl_up_summary(inc, d);
+    if (lane >= d) inc = combine(o, inc);
+  }
+  Summary ex = shfl_up_summary(inc, 1);
+  if (lane == 0) ex = Summary{0, 0, 0, 0};
+  if (lane == 31) sh.warp_sum[warp] = inc;
+  __syncthreads();
+  Summary wpre{0, 0, 0, 0}, agg{0, 0, 0, 0};
+#pragma unroll
+  for (int w = 0; w < kEncThreads / 32; ++w) {
+    const Summary v = sh.warp_sum[w];
+    if (w < warp) wpre = combine(wpre, v);
+    agg = combine(agg, v);
+  }
+  const ScanState S_t = apply(S_s, combine(wpre, ex));  // before my chunk
+  const uint64_t myO = starts ? S_t.O + 1 + ceil32(S_t.b) : S_t.O;
+  const uint32_t myb = starts ? 0u : S_t.b;
+  const ScanState S_e = apply(S_s, agg);
+  const uint64_t w_first = g.starts_record ? S_s.O + 1 + ceil32(S_s.b) : S_s.O + 1 + (S_s.b >> 5);
+  const uint64_t w_last = S_e.O + 1 + ((S_e.b - 1) >> 5);
+  const uint32_t off = (uint32_t)((((uintptr_t)rec_words) >> 2) + w_first) & 3u;
+  if (S_e.b == 0 || w_last < w_first || w_last - w_first + off >= (uint64_t)kEncStageWords + 4) {
+    if (tid == 0) set_error(a.st, HZ_ERR_ARG, 0x207);
+    return;  // uniform
+  }
+  const uint32_t nwords = (uint32_t)(w_last - w_first + 1);
+  const bool skip_last = !g.ends_record && (S_e.b & 31u) != 0;
+  // the delimiter of a record that starts here but ends in a later tile is
+  // written by that later tile
+  const uint32_t skip_i = (!g.ends_record && S_e.O >= w_first)
+                              ? off + (uint32_t)(S_e.O - w_first) : 0xFFFFFFFFu;
+  const uint32_t r_prev = g.starts_record ? 0u : (S_s.b & 31u);
+  for (uint32_t i = tid; i < off + nwords; i += kEncThreads) sh.stage[i] = 0;
+  if (tid == 0 && r_prev) sh.prev_bits = bits_before<false>(sh, a.in, g.lo, r_prev);
+  __syncthreads();
+  if (tid == 0 && r_prev) sh.stage[off] = sh.prev_bits << (32 - r_prev);
+  __syncthreads();
+  uint32_t* st = sh.stage + off;
+  if (g.my_cnt > 0) {
+    if (bits) pack_entries<kPair>(e, st, (uint32_t)(myO + 1 + (myb >> 5) - w_first), myb & 31u);
+    if (ends) {
+      // last chunk of a record: its delimiter is now known
+      if (myO >= w_first) st[myO - w_first] = myb + bits;
+      else rec_words[myO] = myb + bits;
+    }
+    if (starts && (a.flags & kFlagIndex))
+      reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[fast_div(g.g0, a.fdB)] = (uint32_t)myO;
+  }
+  __syncthreads();
+  copy_out(sh.stage, rec_words + (w_first - off), off, off + nwords - (skip_last ? 1u : 0u),
+           skip_i);
+}
+
+// Writer for one thread's words in the general path: words inside the current
+// staging window go to shared memory, others are dropped (another window pass
+// writes them).
 struct Emitter {
   uint32_t* stage;
   uint64_t win_lo, win_hi;
@@ -125,77 +638,26 @@ struct Emitter {
   }
 };
 
+// General path: record starts anywhere in the tile, codes of any length.
 template <bool kLong>
-__device__ __forceinline__ void lookup(const EncShared& sh, uint32_t sym, uint32_t& l,
-                                       uint64_t& c) {
-  if (!kLong) {
-    uint32_t e = sh.entry[sym];
-    l = e & 63u;
-    c = e >> 6;
-  } else {
-    l = sh.len[sym];
-    c = ((uint64_t)sh.code_hi[sym] << 32) | sh.code_lo[sym];
-  }
-}
-
-template <bool kLong>
-__device__ void encode_tile(const EncodeArgs& a, EncShared& sh, uint32_t tile,
-                            const uint8_t* __restrict__ rec_area) {
+__device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, const TileGeom g,
+                                                  uint32_t* rec_words) {
+  const EncodeArgs& a = sh.a;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t n = a.n;
-  const uint32_t B = a.B;
-  const uint64_t tile_lo = (uint64_t)tile * kEncTile;
-  const uint64_t tile_hi = tile_lo + kEncTile < n ? tile_lo + kEncTile : n;
-  const uint64_t g0 = tile_lo + (uint64_t)tid * kEncSymPerThread;
-  const int my_cnt = g0 >= tile_hi ? 0 : (int)((tile_hi - g0) < (uint64_t)kEncSymPerThread
-                                                   ? (tile_hi - g0)
-                                                   : kEncSymPerThread);
-
-  // ---- load 32 symbols (two 16-byte loads when possible)
+  const uint32_t n = (uint32_t)a.n;
+  const uint32_t B = a.fdB.d;
   uint32_t x[kEncSymPerThread / 4];
-  const uint8_t* src = a.in + g0;
-  if (my_cnt == kEncSymPerThread && (((uintptr_t)src) & 15) == 0) {
-    uint4 v0 = __ldg(reinterpret_cast<const uint4*>(src));
-    uint4 v1 = __ldg(reinterpret_cast<const uint4*>(src) + 1);
-    x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
-    x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
-  } else {
-#pragma unroll
-    for (int w = 0; w < kEncSymPerThread / 4; ++w) x[w] = 0;
-    for (int i = 0; i < my_cnt; ++i) x[i >> 2] |= (uint32_t)src[i] << (8 * (i & 3));
-  }
-
-  // ---- segment summary of my symbols (Sec. 2.1's length-summing pass)
-  const uint32_t r0 = (uint32_t)(g0 % B);
-  const uint32_t first_start = r0 == 0 ? 0u : B - r0;  // offset of my first record start
-  Summary s{0, 0, 0, 0};
+  load_symbols(a.in + g.g0, g.my_cnt, x);
   bool bad = false;
-  {
-    uint32_t next_start = first_start;
-#pragma unroll
-    for (int i = 0; i < kEncSymPerThread; ++i) {
-      if (i < my_cnt) {
+  const Summary s = thread_summary(
+      x, g.my_cnt, g.g0, a.fdB,
+      [&](uint32_t v) {
         uint32_t l;
         uint64_t c;
-        lookup<kLong>(sh, sym_of(x, i), l, c);
-        bad |= l == 0;
-        if ((uint32_t)i == next_start) {
-          if (s.has) s.omega += 1 + ceil32(s.tail);
-          s.has = 1;
-          s.tail = 0;
-          next_start += B;
-        }
-        if (s.has) s.tail += l;
-        else s.head += l;
-      }
-    }
-  }
-  if (bad) {
-    set_error(a.st, HZ_ERR_ARG, 0x200);  // a byte without a code (given code table)
-    sh.abort = 1;  // seen by all threads after the scan's barrier
-  }
-
-  // ---- CTA scan of summaries: warp inclusive scan, then across warps
+        lookup<kLong>(sh, v, l, c);
+        return l;
+      },
+      bad);
   Summary inc = s;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -206,135 +668,30 @@ __device__ void encode_tile(const EncodeArgs& a, EncShared& sh, uint32_t tile,
   if (lane == 0) ex = Summary{0, 0, 0, 0};
   if (lane == 31) sh.warp_sum[warp] = inc;
   __syncthreads();
-  Summary wpre{0, 0, 0, 0};
-  for (int w = 0; w < warp; ++w) wpre = combine(wpre, sh.warp_sum[w]);
-  ex = combine(wpre, ex);  // exclusive within the tile
-  if (tid == kEncThreads - 1) sh.agg = combine(wpre, inc);
-  __syncthreads();
-
-  // ---- decoupled look-back across tiles (warp 0)
-  const uint32_t ep = a.epoch << 2;
-  if (warp == 0) {
-    const Summary agg = sh.agg;
-    TileStatus* ts = a.tiles;
-    if (tile == 0) {
-      if (lane == 0) {
-        ScanState init{~0ull, 0};
-        ScanState incl = apply(init, agg);
-        ts[0].pre_O = incl.O;
-        ts[0].pre_b = incl.b;
-        ts[0].has_head = (agg.has << 31) | agg.head;
-        ts[0].omega = agg.omega;
-        ts[0].tail = agg.tail;
-        st_release(&ts[0].flag, ep | 2u);
-        sh.excl = init;
-      }
-    } else {
-      if (lane == 0) {
-        ts[tile].has_head = (agg.has << 31) | agg.head;
-        ts[tile].omega = agg.omega;
-        ts[tile].tail = agg.tail;
-        st_release(&ts[tile].flag, ep | 1u);
-      }
-      Summary acc{0, 0, 0, 0};
-      int64_t j = (int64_t)tile - 1;
-      bool timed_out = false;
-      ScanState result{~0ull, 0};
-      for (;;) {
-        const int64_t idx = j - lane;
-        uint32_t state = 2;  // index -1 stands for the virtual start state
-        Summary mine{0, 0, 0, 0};
-        ScanState pre{~0ull, 0};
-        if (idx >= 0) {
-          uint32_t f = ld_acquire(&ts[idx].flag);
-          uint32_t spins = 0;
-          while ((f & ~3u) != ep || (f & 3u) == 0) {
-            if (++spins > kSpinLimit) { timed_out = true; break; }
-            __nanosleep(32);
-            f = ld_acquire(&ts[idx].flag);
-          }
-          state = timed_out ? 2u : (f & 3u);
-          if (state == 1) {
-            uint32_t hh = ts[idx].has_head;
-            mine = Summary{hh >> 31, hh & 0x7FFFFFFFu, ts[idx].omega, ts[idx].tail};
-          } else if (!timed_out) {
-            pre = ScanState{ts[idx].pre_O, ts[idx].pre_b};
-          }
-        }
-        const uint32_t pmask = __ballot_sync(0xFFFFFFFFu, state == 2);
-        const int stop = pmask ? __ffs(pmask) - 1 : 32;
-        // combine aggregates of lanes stop-1 .. 0 (oldest first), then what came before
-        Summary c{0, 0, 0, 0};
-        for (int l = (stop < 32 ? stop : 32) - 1; l >= 0; --l) c = combine(c, shfl_summary(mine, l));
-        acc = combine(c, acc);
-        if (stop < 32) {
-          ScanState p;
-          p.O = __shfl_sync(0xFFFFFFFFu, pre.O, stop);
-          p.b = __shfl_sync(0xFFFFFFFFu, pre.b, stop);
-          result = apply(p, acc);
-          break;
-        }
-        j -= 32;
-      }
-      if (__any_sync(0xFFFFFFFFu, timed_out)) {
-        if (lane == 0) {
-          set_error(a.st, HZ_ERR_TIMEOUT, 0x201);
-          sh.abort = 1;
-        }
-      }
-      if (lane == 0) {
-        ScanState incl = apply(result, agg);
-        ts[tile].pre_O = incl.O;
-        ts[tile].pre_b = incl.b;
-        st_release(&ts[tile].flag, ep | 2u);
-        sh.excl = result;
-      }
-    }
+  Summary wpre{0, 0, 0, 0}, agg{0, 0, 0, 0};
+  for (int w = 0; w < kEncThreads / 32; ++w) {
+    if (w < warp) wpre = combine(wpre, sh.warp_sum[w]);
+    agg = combine(agg, sh.warp_sum[w]);
   }
-  __syncthreads();
+  ex = combine(wpre, ex);
 
-  // the prefix has been published either way, so successors never wait on an aborted tile
-  if (sh.abort) return;
-
-  // ---- the tile's word range and the words it must not write
-  const ScanState S_s = sh.excl;
-  const Summary agg = sh.agg;
+  const ScanState S_s{a.tiles[tile].pre_O, a.tiles[tile].pre_b};
   const ScanState S_e = apply(S_s, agg);
-  const bool starts_record = (tile_lo % B) == 0;
-  const bool ends_record = (tile_hi % B) == 0 || tile_hi == n;
-  const uint64_t w_first = starts_record ? S_s.O + 1 + ceil32(S_s.b) : S_s.O + 1 + (S_s.b >> 5);
+  const uint64_t w_first = g.starts_record ? S_s.O + 1 + ceil32(S_s.b) : S_s.O + 1 + (S_s.b >> 5);
   const uint64_t w_last = S_e.O + 1 + ((S_e.b - 1) >> 5);
-  const bool skip_last = !ends_record && (S_e.b & 31u) != 0;
-  const bool skip_open = !ends_record && S_e.O >= w_first && S_e.O <= w_last;
-  const uint32_t r_prev = starts_record ? 0u : (S_s.b & 31u);
-  // a tile spans at most 3 words per symbol (delimiter + a 64-bit code), plus slack
+  const bool skip_last = !g.ends_record && (S_e.b & 31u) != 0;
+  const bool skip_open = !g.ends_record && S_e.O >= w_first && S_e.O <= w_last;
+  const uint32_t r_prev = g.starts_record ? 0u : (S_s.b & 31u);
   if (S_e.b == 0 || w_last < w_first || w_last - w_first > 3ull * kEncTile + 64) {
     if (tid == 0) set_error(a.st, HZ_ERR_ARG, 0x204);
-    return;
+    return;  // uniform
   }
-  if (tid == 0) {
-    uint32_t pv = 0;
-    if (r_prev) {
-      // the last r_prev payload bits before this tile, from the preceding symbols
-      uint64_t v = 0;
-      uint32_t got = 0;
-      int64_t jj = (int64_t)tile_lo - 1;
-      while (got < r_prev && jj >= 0) {
-        uint32_t l;
-        uint64_t c;
-        lookup<kLong>(sh, a.in[jj], l, c);
-        if (got < 64) v |= c << got;
-        got += l;
-        --jj;
-      }
-      pv = (uint32_t)(v & ((1u << r_prev) - 1u));
-    }
-    sh.prev_bits = pv;
-  }
-
-  const uint64_t rec_bytes_base = (uint64_t)(rec_area - a.out);
-  const uint64_t nwin = w_last - w_first + 1;
+  if (tid == 0) sh.prev_bits = r_prev ? bits_before<kLong>(sh, a.in, g.lo, r_prev) : 0u;
   const ScanState S_t = apply(S_s, ex);  // state before my first symbol
+  const uint32_t r0 = fast_mod(g.g0, a.fdB);
+  const uint32_t first_start = r0 == 0 ? 0u : B - r0;
+  // one past the last symbol of my first record
+  const uint32_t first_end = (uint32_t)min((uint64_t)g.g0 - r0 + B, (uint64_t)n);
 
   for (uint64_t wlo = w_first; wlo <= w_last; wlo += kEncStageWords) {
     const uint64_t whi = wlo + kEncStageWords < w_last + 1 ? wlo + kEncStageWords : w_last + 1;
@@ -342,8 +699,6 @@ __device__ void encode_tile(const EncodeArgs& a, EncShared& sh, uint32_t tile,
     __syncthreads();
     if (tid == 0 && wlo == w_first && r_prev) sh.stage[0] = sh.prev_bits << (32 - r_prev);
     __syncthreads();
-
-    // ---- pack my codes
     Emitter em{sh.stage, wlo, whi};
     ScanState cur = S_t;
     uint64_t wcur = cur.O + 1 + (cur.b >> 5);
@@ -351,21 +706,17 @@ __device__ void encode_tile(const EncodeArgs& a, EncShared& sh, uint32_t tile,
     bool first_shared = nacc != 0;
     uint64_t acc = 0;
     uint32_t next_start = first_start;
-    uint64_t next_end = (g0 / B + 1) * (uint64_t)B;  // one past the last symbol of my first record
-    if (next_end > n) next_end = n;
+    uint32_t next_end = first_end;
 #pragma unroll
     for (int i = 0; i < kEncSymPerThread; ++i) {
-      if (i < my_cnt) {
+      if (i < g.my_cnt) {
         if ((uint32_t)i == next_start) {
           if (nacc) em.put(wcur, (uint32_t)(acc << (32 - nacc)), true);
           cur.O = cur.O + 1 + ceil32(cur.b);
           cur.b = 0;
-          const uint64_t k = (g0 + i) / B;
-          if ((a.flags & kFlagIndex) && wlo == w_first) {
-            if (cur.O > 0xFFFFFFFFull) set_error(a.st, HZ_ERR_CAPACITY, 0x202);
-            else if (kHeaderBytes + 4 * (k + 1) <= a.out_cap)
-              reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[k] = (uint32_t)cur.O;
-          }
+          if ((a.flags & kFlagIndex) && wlo == w_first)
+            reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[fast_div(g.g0 + i, a.fdB)] =
+                (uint32_t)cur.O;
           wcur = cur.O + 1;
           nacc = 0;
           acc = 0;
@@ -376,8 +727,7 @@ __device__ void encode_tile(const EncodeArgs& a, EncShared& sh, uint32_t tile,
         uint64_t c;
         lookup<kLong>(sh, sym_of(x, i), l, c);
         if (kLong && l > 32) {
-          // emit the high (l - 32) bits, then the low 32
-          uint32_t lh = l - 32;
+          const uint32_t lh = l - 32;
           acc = (acc << lh) | (c >> 32);
           nacc += lh;
           if (nacc >= 32) {
@@ -398,85 +748,100 @@ __device__ void encode_tile(const EncodeArgs& a, EncShared& sh, uint32_t tile,
           }
         }
         cur.b += l;
-        if (g0 + i + 1 == next_end) {
+        if (g.g0 + (uint32_t)i + 1 == next_end) {
           // last symbol of a record: its delimiter is now known
-          if (cur.O >= wlo && cur.O < whi) {
-            sh.stage[cur.O - wlo] = cur.b;
-          } else if (cur.O < w_first && wlo == w_first) {
-            const uint64_t off = rec_bytes_base + 4 * cur.O;
-            if (off + 4 <= a.out_cap) *reinterpret_cast<uint32_t*>(a.out + off) = cur.b;
-          }
-          next_end += B;
-          if (next_end > n) next_end = n;
+          if (cur.O >= wlo && cur.O < whi) sh.stage[cur.O - wlo] = cur.b;
+          else if (cur.O < w_first && wlo == w_first) rec_words[cur.O] = cur.b;
+          next_end = (uint32_t)min((uint64_t)next_end + B, (uint64_t)n);
         }
       }
     }
-    if (nacc && my_cnt) em.put(wcur, (uint32_t)(acc << (32 - nacc)), true);
+    if (nacc && g.my_cnt) em.put(wcur, (uint32_t)(acc << (32 - nacc)), true);
     __syncthreads();
-
-    // ---- write the window out (coalesced)
     const uint64_t cnt_w = whi - wlo;
     for (uint64_t i = tid; i < cnt_w; i += kEncThreads) {
       const uint64_t w = wlo + i;
       if ((skip_last && w == w_last) || (skip_open && w == S_e.O)) continue;
-      const uint64_t off = rec_bytes_base + 4 * w;
-      if (off + 4 <= a.out_cap) *reinterpret_cast<uint32_t*>(a.out + off) = sh.stage[i];
+      rec_words[w] = sh.stage[i];
     }
     __syncthreads();
   }
-  (void)nwin;
+}
 
-  // ---- the thread holding the last symbol knows the stream size
-  if (my_cnt && g0 + my_cnt == n) {
-    const uint64_t total = rec_bytes_base + 4 * (S_e.O + 1 + ceil32(S_e.b));
-    *a.out_len = total;
-    if (total > a.out_cap) set_error(a.st, HZ_ERR_CAPACITY, 0x203);
+// Tile loops, one per path, each compiled on its own so that the common
+// paths keep their registers.
+template <int kMode>  // 0: single-record/chunked with pairs, 1: same with single codes
+__device__ __forceinline__ void pack_tiles_fast(const EncodeArgs& a, PackShared& sh,
+                                             uint32_t* rec_words) {
+  const bool chunked_ok = a.fdB.d % kEncSymPerThread == 0;
+  for (uint32_t i = blockIdx.x; i < a.ntiles; i += gridDim.x) {
+    const uint32_t tile = a.ntiles - 1 - i;  // last tiles first: their input is still in L2
+    const TileGeom g = tile_geom(tile, (uint32_t)a.n, a.fdB);
+    if (!g.interior_start) pack_tile_single<kMode == 0>(sh, tile, g, rec_words);
+    else if (chunked_ok) pack_tile_chunked<kMode == 0>(sh, tile, g, rec_words);
+    else pack_tile_general<false>(sh, tile, g, rec_words);
+    __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(kEncThreads, 2) encode_kernel(EncodeArgs a) {
+__device__ __forceinline__ void pack_tiles_long(const EncodeArgs& a, PackShared& sh,
+                                             uint32_t* rec_words) {
+  for (uint32_t i = blockIdx.x; i < a.ntiles; i += gridDim.x) {
+    const uint32_t tile = a.ntiles - 1 - i;
+    pack_tile_general<true>(sh, tile, tile_geom(tile, (uint32_t)a.n, a.fdB), rec_words);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kEncThreads, 3) encode_pack_kernel(EncodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  EncShared& sh = *reinterpret_cast<EncShared*>(smem_raw);
+  PackShared& sh = *reinterpret_cast<PackShared*>(smem_raw);
   const CodeTable* ct = &a.st->codes;
+  // size, capacity, time-out or code errors were found before packing
+  if (!a.st->enc_ok || a.st->error) return;
   const uint32_t maxlen = ct->maxlen;
-  if (maxlen > (uint32_t)kMaxLen) return;  // code construction failed; already reported
-  for (int s = threadIdx.x; s < 256; s += blockDim.x) {
-    uint32_t l = ct->len[s];
-    uint64_t c = ct->code[s];
+  for (int s = threadIdx.x; s < 256; s += kEncThreads) {
+    const uint32_t l = ct->len[s];
+    const uint64_t c = ct->code[s];
     sh.len[s] = l;
     sh.code_lo[s] = (uint32_t)c;
     sh.code_hi[s] = (uint32_t)(c >> 32);
     sh.entry[s] = (uint32_t)(c << 6) | l;
   }
-  const uint8_t* rec_area = a.out + kHeaderBytes + ((a.flags & kFlagIndex) ? 4ull * a.nb : 0ull);
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      sh.tile = atomicAdd(&a.st->tile_counter, 1u);
-      sh.abort = 0;
-    }
-    __syncthreads();
-    const uint32_t tile = sh.tile;
-    if (tile >= a.ntiles) break;
-    if (maxlen <= 26) encode_tile<false>(a, sh, tile, rec_area);
-    else encode_tile<true>(a, sh, tile, rec_area);
-  }
+  if (threadIdx.x == 0) sh.a = a;
+  __syncthreads();
+  uint32_t* rec_words = reinterpret_cast<uint32_t*>(
+      a.out + kHeaderBytes + ((a.flags & kFlagIndex) ? 4ull * a.nb : 0ull));
+  if (maxlen <= 16) pack_tiles_fast<0>(a, sh, rec_words);
+  else if (maxlen <= 26) pack_tiles_fast<1>(a, sh, rec_words);
+  else pack_tiles_long(a, sh, rec_words);
 }
 
-cudaError_t launch_encode(const EncodeArgs& a, int num_sms, cudaStream_t s) {
+cudaError_t launch_encode_summary(const EncodeArgs& a, int num_sms, cudaStream_t s) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_summary_kernel, kEncThreads, 0);
+  const uint64_t grid = (uint64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+  encode_summary_kernel<<<(unsigned)(grid < a.ntiles ? grid : a.ntiles), kEncThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_scan(const EncodeArgs& a, cudaStream_t s) {
+  const unsigned grid = (a.ntiles + kScanTilesPerCta - 1) / kScanTilesPerCta;
+  encode_scan_kernel<<<grid, kScanThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_pack(const EncodeArgs& a, int num_sms, cudaStream_t s) {
   static bool configured = false;
-  const int smem = (int)sizeof(EncShared);
+  const int smem = (int)sizeof(PackShared);
   if (!configured) {
-    cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(encode_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     configured = true;
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_kernel, kEncThreads, smem);
-  if (per_sm < 1) per_sm = 1;
-  uint64_t grid = (uint64_t)num_sms * per_sm;
-  if (grid > a.ntiles) grid = a.ntiles;
-  if (grid < 1) grid = 1;
-  encode_kernel<<<(unsigned)grid, kEncThreads, smem, s>>>(a);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_pack_kernel, kEncThreads, smem);
+  const uint64_t grid = (uint64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+  encode_pack_kernel<<<(unsigned)(grid < a.ntiles ? grid : a.ntiles), kEncThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

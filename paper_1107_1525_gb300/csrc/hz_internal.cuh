@@ -22,7 +22,7 @@ constexpr uint32_t kSpinLimit = 1u << 20;
 constexpr int kEncThreads = 256;
 constexpr int kEncSymPerThread = 32;
 constexpr int kEncTile = kEncThreads * kEncSymPerThread;  // 8192 symbols
-constexpr int kEncStageWords = 4096 + 64;                 // staging window
+constexpr int kEncStageWords = kEncTile + 64;             // staging window (words)
 
 // Decode-table width bounds.
 constexpr int kLutMinBits = 8;
@@ -37,25 +37,36 @@ struct CodeTable {
   uint64_t code[256];
 };
 
-// Encode decoupled look-back record for one tile (32 bytes).  `flag` holds
-// (epoch << 2) | state; state 1 = aggregate ready, 2 = inclusive prefix ready.
+// Per-tile record of the encoder: the tile's summary (written by the
+// length-sum pass) and its exclusive scan state (written by the scan).
 struct TileStatus {
-  uint32_t flag;
-  uint32_t has_head;        // bit 31: the tile holds a block start; low 31: head bits
-  uint32_t omega;           // words of complete blocks inside the tile
-  uint32_t tail;            // bits of the open block at the tile's end
-  uint64_t pre_O;           // inclusive prefix: header word of the open block
-  uint32_t pre_b;           // inclusive prefix: bits in the open block
-  uint32_t pad;
+  uint32_t has_head;        // bit 31: the tile holds a record start; low 31: head bits
+  uint32_t omega;           // words of records that start and end inside the tile
+  uint32_t tail;            // bits of the tile's last record
+  uint32_t pad0;
+  uint64_t pre_O;           // exclusive state: word index of the open record's delimiter
+  uint32_t pre_b;           // exclusive state: payload bits already in that record
+  uint32_t pad1;
 };
+
+// The encoder's tile scan runs in CTAs of kScanTilesPerCta tiles; n < 2^32
+// bounds their number.
+constexpr int kScanTilesPerCta = 4096;
+constexpr int kMaxScanCtas = (int)((1ull << 32) / kEncTile / kScanTilesPerCta);  // 128
 
 struct DevState {
   uint32_t error;           // first error recorded (as -hz_status), 0 = none
   uint32_t error_where;     // kernel-specific detail for debugging
-  uint32_t tile_counter;    // dynamic tile ticket of the encode kernel
-  uint32_t block_counter;   // dynamic block ticket of the decode kernel
+  uint32_t dec_deferred;    // blocks the fast decode kernel left to the generic one
+  uint32_t pad0;
+  // ---- cleared before every compress (one memset from here to `codes`)
+  uint32_t tile_counter;    // ticket of the scan CTAs
+  uint32_t enc_ok;          // set by the encoder's scan: 1 when the stream fits the output
   uint32_t hist[256];
+  uint32_t scan_flags[kMaxScanCtas];  // 1 = aggregate published, 2 = inclusive prefix
+  // ---- not cleared
   CodeTable codes;
+  TileStatus scan_aux[kMaxScanCtas];  // per scan CTA: aggregate and inclusive prefix
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -80,13 +91,42 @@ __device__ __forceinline__ uint32_t ceil32(uint64_t bits) { return (uint32_t)((b
 enum KernelId : int32_t {
   K_HIST = 0,
   K_BUILD = 1,
-  K_ENCODE = 2,
-  K_DECODE_SETUP = 3,
-  K_DECODE = 4,
-  K_INDEX_CHASE = 5,
-  K_BATCH = 6,
+  K_ENC_SUMMARY = 2,
+  K_ENC_SCAN = 3,
+  K_ENC_PACK = 4,
+  K_DECODE_SETUP = 5,
+  K_DECODE = 6,
+  K_DECODE_GENERIC = 7,
+  K_BATCH = 8,
   K_COUNT
 };
+
+// Division of 32-bit values by a divisor fixed per launch, with one
+// multiply-high and two shifts (Granlund and Montgomery, "Division by
+// Invariant Integers using Multiplication", PLDI 1994, Fig. 4.1).
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while (l < 32 && (1ull << l) < d) ++l;  // l = ceil(log2 d)
+  FastDiv f;
+  f.d = d;
+  f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t x, const FastDiv& f) {
+  const uint32_t t = __umulhi(f.m, x);
+  return (t + ((x - t) >> f.s1)) >> f.s2;
+}
+
+__device__ __forceinline__ uint32_t fast_mod(uint32_t x, const FastDiv& f) {
+  return x - fast_div(x, f) * f.d;
+}
 
 struct EncodeArgs {
   const uint8_t* in;
@@ -100,7 +140,7 @@ struct EncodeArgs {
   DevState* st;
   TileStatus* tiles;
   uint32_t ntiles;
-  uint32_t epoch;
+  FastDiv fdB;              // division by B
 };
 
 struct DecodeArgs {
@@ -125,11 +165,16 @@ struct LenParam {
 cudaError_t launch_build_codes(DevState* st, int from_hist, const LenParam& given, uint64_t n,
                                uint32_t B, uint32_t nb, uint32_t flags, uint8_t* out,
                                uint64_t out_cap, uint64_t* out_len, cudaStream_t s);
-cudaError_t launch_encode(const EncodeArgs& a, int num_sms, cudaStream_t s);
+// The encoder's three launches: length-sum pass, scan, packing.
+cudaError_t launch_encode_summary(const EncodeArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_encode_scan(const EncodeArgs& a, cudaStream_t s);
+cudaError_t launch_encode_pack(const EncodeArgs& a, int num_sms, cudaStream_t s);
 struct DecTables;
 size_t dec_tables_bytes();
 cudaError_t launch_decode_setup(const DecodeArgs& a, DecTables* T, cudaStream_t s);
 cudaError_t launch_decode_blocks(const DecodeArgs& a, const DecTables* T, int threads, int num_sms,
                                  cudaStream_t s);
+cudaError_t launch_decode_generic(const DecodeArgs& a, const DecTables* T, int num_sms,
+                                  cudaStream_t s);
 
 }  // namespace hz

@@ -26,7 +26,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};  // device address of the array, per device
-uint32_t g_epoch[kMaxDevices] = {};
 
 // Move the status word into the caller's d_status and clear it for the next call.
 __global__ void noalloc_finish_kernel(DevState* st, int32_t* d_status) {
@@ -47,7 +46,6 @@ extern "C" hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HZ_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  uint32_t epoch;
   unsigned char* base;
   {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -66,14 +64,6 @@ extern "C" hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32
       g_scratch_ptr[dev] = (unsigned char*)p;
     }
     base = g_scratch_ptr[dev];
-    // the scan records carry a 30-bit call epoch, so they need no clearing per call
-    g_epoch[dev] += 1;
-    if (g_epoch[dev] >= (1u << 30)) {
-      if (cudaMemsetAsync(base + kStateBytes, 0, kScratchBytes - kStateBytes, s) != cudaSuccess)
-        return HZ_ERR_CUDA;
-      g_epoch[dev] = 1;
-    }
-    epoch = g_epoch[dev];
   }
   DevState* st = reinterpret_cast<DevState*>(base);
   TileStatus* tiles = reinterpret_cast<TileStatus*>(base + kStateBytes);
@@ -108,8 +98,10 @@ extern "C" hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32
     a.st = st;
     a.tiles = tiles;
     a.ntiles = ntiles;
-    a.epoch = epoch;
-    if (launch_encode(a, num_sms, s) != cudaSuccess) return HZ_ERR_CUDA;
+    a.fdB = make_fastdiv(B);
+    if (launch_encode_summary(a, num_sms, s) != cudaSuccess ||
+        launch_encode_scan(a, s) != cudaSuccess || launch_encode_pack(a, num_sms, s) != cudaSuccess)
+      return HZ_ERR_CUDA;
   }
   noalloc_finish_kernel<<<1, 1, 0, s>>>(st, d_status);
   return cudaGetLastError() == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;

@@ -49,8 +49,8 @@ def _gpu_compress(hz, ctx, x_dev, B, codes=None, cap=None, index=True):
 
 
 def _gpu_decompress(hz, ctx, s_dev, cap=None):
-    hdr = oracle.parse_header(s_dev[:280].cpu().numpy()) if s_dev.numel() >= 280 else {"n": 0}
-    cap = hdr["n"] if cap is None else cap
+    if cap is None:
+        cap = oracle.parse_header(s_dev[:280].cpu().numpy())["n"]
     out = torch.empty(max(cap, 1), dtype=torch.uint8, device=DEV)
     out_len = torch.zeros(1, dtype=torch.int64, device=DEV)
     hz.hz_decompress(ctx, s_dev, s_dev.numel(), out, cap, out_len)
