@@ -44,11 +44,14 @@ struct hz_ctx {
   int opt_lut_bits = 12;
   int opt_dec_threads = 256;
   int opt_autotune = 1;
+  uint32_t tuned_B[4] = {0, 0, 0, 0};  // per size class; 0 = not tuned
   uint64_t launches = 0;
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
   BatchState* batch = nullptr;
 };
+
+void hz_tune_load_cache(hz_ctx* c);
 
 namespace {
 
@@ -107,8 +110,12 @@ hz_status grow(void** p, uint64_t* cap, uint64_t need) {
   return HZ_OK;
 }
 
+int size_class(uint64_t n) {
+  return n <= (64u << 10) ? 0 : n <= (1u << 20) ? 1 : n <= (16u << 20) ? 2 : 3;
+}
+
 uint32_t autotuned_block(hz_ctx* c, uint64_t n) {
-  (void)c;
+  if (c->opt_autotune && c->tuned_B[size_class(n)]) return c->tuned_B[size_class(n)];
   return hz_batch_tuned_block_size(n);
 }
 
@@ -149,6 +156,7 @@ hz_status hz_create(hz_ctx** out, int device, uint64_t mem_budget_bytes) {
     return HZ_ERR_NOMEM;
   }
   c->batch = hz_batch_create(c->device, c->num_sms, mem_budget_bytes);
+  hz_tune_load_cache(c);
   *out = c;
   return HZ_OK;
 }
@@ -207,6 +215,10 @@ hz_status hz_set_option(hz_ctx* c, int key, int64_t v) {
       if (v != 0 && v != 1) return HZ_ERR_ARG;
       c->opt_autotune = (int)v;
       return HZ_OK;
+    case HZ_OPT_BATCH_PLAIN:
+      if (v != 0 && v != 1) return HZ_ERR_ARG;
+      hz_batch_set_plain(c->batch, v != 0);
+      return HZ_OK;
     default:
       return HZ_ERR_ARG;
   }
@@ -220,11 +232,16 @@ int64_t hz_get_option(hz_ctx* c, int key) {
     case HZ_OPT_DECODE_LUT_BITS: return c->opt_lut_bits;
     case HZ_OPT_DECODE_THREADS: return c->opt_dec_threads;
     case HZ_OPT_AUTOTUNE: return c->opt_autotune;
+    case HZ_OPT_BATCH_PLAIN: return hz_batch_plain(c->batch) ? 1 : 0;
     default: return -1;
   }
 }
 
 uint64_t hz_launch_count(hz_ctx* c) { return c ? c->launches : 0; }
+
+uint32_t hz_tuned_block_size(hz_ctx* c, uint64_t n) {
+  return c ? autotuned_block(c, n) : hz_batch_tuned_block_size(n);
+}
 
 const char* hz_kernel_name(int32_t id) {
   static const char* names[] = {"histogram",   "build_codes",  "encode_summary", "encode_scan",
@@ -481,3 +498,13 @@ hz_status hz_poll(hz_ctx* c, uint64_t ticket, int64_t timeout_ns, hz_status* per
 }  // extern "C"
 
 hz::DevState* hz_ctx_state(hz_ctx* c) { return c->d_state; }
+uint32_t hz_ctx_block_size(hz_ctx* c, uint64_t n) { return autotuned_block(c, n); }
+void hz_ctx_set_tuned(hz_ctx* c, const uint32_t* B, int lut_bits) {
+  for (int k = 0; k < 4; ++k) c->tuned_B[k] = B[k];
+  if (lut_bits) c->opt_lut_bits = lut_bits;
+}
+void hz_ctx_get_tuned(hz_ctx* c, uint32_t* B, int* lut_bits) {
+  for (int k = 0; k < 4; ++k) B[k] = c->tuned_B[k];
+  *lut_bits = c->opt_lut_bits;
+}
+int hz_ctx_device(hz_ctx* c) { return c->device; }

@@ -1,7 +1,20 @@
-// hz_batch.cu -- hz_submit / hz_poll: batches are queued in submission order,
-// admitted against the context's device-memory budget, and run on the batch
-// stream; every request's status and result size land in device arrays that
-// hz_poll copies back once the batch's completion event has fired.
+// hz_batch.cu -- host side of hz_submit / hz_poll.
+//
+// Batches are queued in submission order and admitted against the context's
+// device-memory budget (request buffers plus the batch's scratch).  An
+// admitted batch takes one of kSlots slots; each slot has its own stream,
+// device scratch (per-request state, encoder tile records, decode tables),
+// pinned descriptor staging and a CUDA graph of the batched kernel sequence
+// (hz_batch_kernels.cu), captured once per scratch allocation and replayed for
+// every batch.  Batches in different slots run concurrently on the device, so
+// requests that arrive while others are on the GPU are admitted as slots and
+// memory free up, and their work overlaps.
+//
+// Plain mode (HZ_OPT_BATCH_PLAIN = 1) runs the same requests one after another
+// through hz_compress / hz_decompress -- one launch sequence per buffer -- as
+// the baseline the batched path is measured against.
+#include <string.h>
+
 #include <chrono>
 #include <deque>
 #include <map>
@@ -9,23 +22,56 @@
 #include <vector>
 
 #include "hz_batch.h"
-#include "hz_internal.cuh"
+#include "hz_batch_dev.h"
+
+using namespace hz;
 
 namespace {
+
+constexpr int kSlots = 3;
 
 struct Job {
   uint64_t ticket = 0;
   std::vector<hz_request> reqs;
   uint64_t footprint = 0;
-  int32_t* d_status = nullptr;   // per request
-  uint64_t* d_lens = nullptr;    // per request
-  cudaEvent_t done = nullptr;
+  int slot = -1;
+  bool plain = false;
   bool launched = false;
+  bool done = false;
   hz_status launch_status = HZ_OK;
+  std::vector<hz_status> status;
+  std::vector<uint64_t> lens;
+  // plain mode: per-request device status / length
+  int32_t* d_status = nullptr;
+  uint64_t* d_lens = nullptr;
+  cudaEvent_t plain_done = nullptr;
 };
 
-// Copy the context's status word into one request's slot and clear it.
-__global__ void snapshot_status_kernel(hz::DevState* st, int32_t* dst) {
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  Job* job = nullptr;
+  // capacities
+  uint32_t req_cap = 0;
+  uint64_t tiles_cap = 0;
+  // device
+  BatchCtl* d_ctl = nullptr;
+  BatchComp* d_comps = nullptr;
+  BatchDecomp* d_decomps = nullptr;
+  BatchResult* d_results = nullptr;
+  DevState* d_states = nullptr;
+  DecTables* d_dec = nullptr;
+  uint64_t* d_lens = nullptr;
+  TileStatus* d_tiles = nullptr;
+  // pinned host
+  BatchCtl* h_ctl = nullptr;
+  BatchComp* h_comps = nullptr;
+  BatchDecomp* h_decomps = nullptr;
+  BatchResult* h_results = nullptr;
+};
+
+__global__ void snapshot_status_kernel(DevState* st, int32_t* dst) {
   dst[0] = -(int32_t)st->error;
   st->error = 0;
   st->error_where = 0;
@@ -39,81 +85,326 @@ struct BatchState {
   uint64_t budget = 0;
   uint64_t admitted = 0;
   uint64_t next_ticket = 1;
-  cudaStream_t stream = nullptr;
-  std::deque<Job*> queue;          // submitted, in order (launched ones first)
-  std::map<uint64_t, Job*> jobs;
+  bool plain = false;
   hz_ctx* ctx = nullptr;
+  cudaStream_t plain_stream = nullptr;
+  Slot slots[kSlots];
+  std::deque<Job*> queue;  // submitted, not yet finished, in order
+  std::map<uint64_t, Job*> jobs;
 };
-
-
-BatchState* hz_batch_create(int device, int num_sms, uint64_t mem_budget) {
-  BatchState* b = new BatchState();
-  b->device = device;
-  b->num_sms = num_sms;
-  b->budget = mem_budget;
-  cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-  return b;
-}
-
-static void free_job(Job* j) {
-  cudaFree(j->d_status);
-  cudaFree(j->d_lens);
-  if (j->done) cudaEventDestroy(j->done);
-  delete j;
-}
-
-void hz_batch_destroy(BatchState* b) {
-  if (!b) return;
-  cudaStreamSynchronize(b->stream);
-  for (auto& kv : b->jobs) free_job(kv.second);
-  cudaStreamDestroy(b->stream);
-  delete b;
-}
-
-uint32_t hz_batch_tuned_block_size(uint64_t n) {
-  // one record per 64 KiB keeps the per-block overhead below 0.1 % (Sec. 2.1);
-  // small inputs take smaller blocks so that they still spread over many CTAs
-  if (n <= (64u << 10)) return 4096;
-  if (n <= (4u << 20)) return 16384;
-  return 65536;
-}
 
 extern "C" hz_status hz_compress(hz_ctx*, const uint8_t*, uint64_t, uint32_t, const hz_codes*,
                                  uint8_t*, uint64_t, uint64_t*, void*);
 extern "C" hz_status hz_decompress(hz_ctx*, const uint8_t*, uint64_t, uint8_t*, uint64_t,
                                    uint64_t*, void*);
 hz::DevState* hz_ctx_state(hz_ctx* c);
+uint32_t hz_ctx_block_size(hz_ctx* c, uint64_t n);
 
-static hz_status launch_job(BatchState* b, Job* j) {
+static void free_slot_buffers(Slot& s) {
+  if (s.graph) cudaGraphExecDestroy(s.graph);
+  s.graph = nullptr;
+  cudaFree(s.d_ctl);
+  cudaFree(s.d_comps);
+  cudaFree(s.d_decomps);
+  cudaFree(s.d_results);
+  cudaFree(s.d_states);
+  cudaFree(s.d_dec);
+  cudaFree(s.d_lens);
+  cudaFree(s.d_tiles);
+  cudaFreeHost(s.h_ctl);
+  cudaFreeHost(s.h_comps);
+  cudaFreeHost(s.h_decomps);
+  cudaFreeHost(s.h_results);
+  s.d_ctl = nullptr;
+  s.d_comps = nullptr;
+  s.d_decomps = nullptr;
+  s.d_results = nullptr;
+  s.d_states = nullptr;
+  s.d_dec = nullptr;
+  s.d_lens = nullptr;
+  s.d_tiles = nullptr;
+  s.h_ctl = nullptr;
+  s.h_comps = nullptr;
+  s.h_decomps = nullptr;
+  s.h_results = nullptr;
+  s.req_cap = 0;
+  s.tiles_cap = 0;
+}
+
+// Make the slot hold `reqs` requests and `tiles` encoder tiles; re-captures
+// the slot's graph after any reallocation.
+static hz_status ensure_slot(BatchState* b, Slot& s, uint32_t reqs, uint64_t tiles) {
+  if (reqs <= s.req_cap && tiles <= s.tiles_cap && s.graph) return HZ_OK;
+  uint32_t rc = s.req_cap, need_r = reqs ? reqs : 1;
+  uint64_t tc = s.tiles_cap, need_t = tiles ? tiles : 1;
+  if (need_r > rc) {
+    rc = rc ? rc : 64;
+    while (rc < need_r) rc *= 2;
+  }
+  if (need_t > tc) {
+    tc = tc ? tc : 4096;
+    while (tc < need_t) tc *= 2;
+  }
+  cudaStreamSynchronize(s.stream);
+  free_slot_buffers(s);
+  bool ok = cudaMalloc(&s.d_ctl, sizeof(BatchCtl)) == cudaSuccess &&
+            cudaMalloc(&s.d_comps, rc * sizeof(BatchComp)) == cudaSuccess &&
+            cudaMalloc(&s.d_decomps, rc * sizeof(BatchDecomp)) == cudaSuccess &&
+            cudaMalloc(&s.d_results, rc * sizeof(BatchResult)) == cudaSuccess &&
+            cudaMalloc(&s.d_states, rc * sizeof(DevState)) == cudaSuccess &&
+            cudaMalloc(&s.d_dec, rc * batch_dec_tables_bytes()) == cudaSuccess &&
+            cudaMalloc(&s.d_lens, rc * sizeof(uint64_t)) == cudaSuccess &&
+            cudaMalloc(&s.d_tiles, tc * sizeof(TileStatus)) == cudaSuccess &&
+            cudaHostAlloc(&s.h_ctl, sizeof(BatchCtl), cudaHostAllocDefault) == cudaSuccess &&
+            cudaHostAlloc(&s.h_comps, rc * sizeof(BatchComp), cudaHostAllocDefault) == cudaSuccess &&
+            cudaHostAlloc(&s.h_decomps, rc * sizeof(BatchDecomp), cudaHostAllocDefault) ==
+                cudaSuccess &&
+            cudaHostAlloc(&s.h_results, rc * sizeof(BatchResult), cudaHostAllocDefault) ==
+                cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_slot_buffers(s);
+    return HZ_ERR_NOMEM;
+  }
+  s.req_cap = rc;
+  s.tiles_cap = tc;
+  // the graph: descriptors in, the kernel sequence, results out
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return HZ_ERR_CUDA;
+  cudaMemcpyAsync(s.d_ctl, s.h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.d_comps, s.h_comps, rc * sizeof(BatchComp), cudaMemcpyHostToDevice, s.stream);
+  cudaMemcpyAsync(s.d_decomps, s.h_decomps, rc * sizeof(BatchDecomp), cudaMemcpyHostToDevice,
+                  s.stream);
+  BatchLaunch L{s.d_ctl, s.d_comps, s.d_decomps, s.d_results, b->num_sms};
+  batch_enqueue(L, s.stream);
+  cudaMemcpyAsync(s.h_results, s.d_results, rc * sizeof(BatchResult), cudaMemcpyDeviceToHost,
+                  s.stream);
+  if (cudaStreamEndCapture(s.stream, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return HZ_ERR_CUDA;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&s.graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s.graph = nullptr;
+    return HZ_ERR_CUDA;
+  }
+  return HZ_OK;
+}
+
+BatchState* hz_batch_create(int device, int num_sms, uint64_t mem_budget) {
+  BatchState* b = new BatchState();
+  b->device = device;
+  b->num_sms = num_sms;
+  b->budget = mem_budget;
+  batch_configure();
+  cudaStreamCreateWithFlags(&b->plain_stream, cudaStreamNonBlocking);
+  for (Slot& s : b->slots) {
+    cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+  }
+  return b;
+}
+
+static void free_job(Job* j) {
+  cudaFree(j->d_status);
+  cudaFree(j->d_lens);
+  if (j->plain_done) cudaEventDestroy(j->plain_done);
+  delete j;
+}
+
+void hz_batch_destroy(BatchState* b) {
+  if (!b) return;
+  for (Slot& s : b->slots) {
+    cudaStreamSynchronize(s.stream);
+    free_slot_buffers(s);
+    cudaEventDestroy(s.done);
+    cudaStreamDestroy(s.stream);
+  }
+  cudaStreamSynchronize(b->plain_stream);
+  cudaStreamDestroy(b->plain_stream);
+  for (auto& kv : b->jobs) free_job(kv.second);
+  delete b;
+}
+
+void hz_batch_set_plain(BatchState* b, bool plain) { b->plain = plain; }
+bool hz_batch_plain(BatchState* b) { return b->plain; }
+
+uint32_t hz_batch_tuned_block_size(uint64_t n) {
+  // one record per 64 KiB keeps the per-block overhead below 0.1 % (Sec. 2.1);
+  // small inputs take smaller blocks so that they still spread over many warps
+  if (n <= (64u << 10)) return 4096;
+  if (n <= (4u << 20)) return 16384;
+  return 65536;
+}
+
+// ----------------------------------------------------------- plain baseline
+static hz_status launch_plain(BatchState* b, Job* j) {
   const uint32_t n = (uint32_t)j->reqs.size();
+  const uint32_t m = n ? n : 1;
+  if (cudaMalloc(&j->d_status, m * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&j->d_lens, m * sizeof(uint64_t)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&j->plain_done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return HZ_ERR_NOMEM;
+  }
+  cudaMemsetAsync(j->d_status, 0, m * sizeof(int32_t), b->plain_stream);
+  cudaMemsetAsync(j->d_lens, 0, m * sizeof(uint64_t), b->plain_stream);
   for (uint32_t i = 0; i < n; ++i) {
     const hz_request& r = j->reqs[i];
     hz_status st;
     if (r.op == HZ_OP_COMPRESS)
       st = hz_compress(b->ctx, r.d_src, r.src_len, r.block_size, nullptr, r.d_dst, r.dst_cap,
-                       j->d_lens + i, b->stream);
+                       j->d_lens + i, b->plain_stream);
     else
       st = hz_decompress(b->ctx, r.d_src, r.src_len, r.d_dst, r.dst_cap, j->d_lens + i,
-                         b->stream);
+                         b->plain_stream);
     if (st != HZ_OK) return st;
-    snapshot_status_kernel<<<1, 1, 0, b->stream>>>(hz_ctx_state(b->ctx), j->d_status + i);
+    snapshot_status_kernel<<<1, 1, 0, b->plain_stream>>>(hz_ctx_state(b->ctx), j->d_status + i);
   }
-  if (cudaEventRecord(j->done, b->stream) != cudaSuccess) return HZ_ERR_CUDA;
-  j->launched = true;
-  b->admitted += j->footprint;
+  return cudaEventRecord(j->plain_done, b->plain_stream) == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;
+}
+
+// ----------------------------------------------------------- batched path
+static uint64_t scratch_bytes(const std::vector<hz_request>& reqs) {
+  uint64_t t = 0;
+  for (const hz_request& r : reqs) {
+    t += sizeof(DevState) + sizeof(BatchComp) + sizeof(BatchDecomp) + 16;
+    if (r.op == HZ_OP_COMPRESS) t += ((r.src_len + kEncTile - 1) / kEncTile) * sizeof(TileStatus);
+    else t += batch_dec_tables_bytes();
+  }
+  return t;
+}
+
+static hz_status launch_batched(BatchState* b, Job* j, int slot_index) {
+  Slot& s = b->slots[slot_index];
+  const uint32_t n = (uint32_t)j->reqs.size();
+  uint64_t tiles = 0;
+  for (const hz_request& r : j->reqs)
+    if (r.op == HZ_OP_COMPRESS) tiles += (r.src_len + kEncTile - 1) / kEncTile;
+  hz_status st = ensure_slot(b, s, n, tiles);
+  if (st != HZ_OK) return st;
+  BatchCtl ctl;
+  memset(&ctl, 0, sizeof(ctl));
+  uint32_t nc = 0, nd = 0, hist_units = 0, tile_base = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const hz_request& r = j->reqs[i];
+    if (r.op == HZ_OP_COMPRESS) {
+      BatchComp& c = s.h_comps[nc];
+      memset(&c, 0, sizeof(c));
+      const uint32_t B = r.block_size ? r.block_size : hz_ctx_block_size(b->ctx, r.src_len);
+      c.src = r.d_src;
+      c.n = r.src_len;
+      c.dst = r.d_dst;
+      c.cap = r.dst_cap;
+      c.B = B;
+      c.nb = (uint32_t)((r.src_len + B - 1) / B);
+      c.ntiles = (uint32_t)((r.src_len + kEncTile - 1) / kEncTile);
+      c.flags = kFlagIndex;
+      c.fdB = make_fastdiv(B);
+      c.st = s.d_states + i;
+      c.tiles = s.d_tiles + tile_base;
+      c.out_len = s.d_lens + i;
+      c.hist_base = hist_units;
+      c.tile_base = tile_base;
+      c.req = i;
+      hist_units += (uint32_t)((r.src_len + kBatchHistChunk - 1) / kBatchHistChunk);
+      tile_base += c.ntiles;
+      ++nc;
+    } else {
+      BatchDecomp& d = s.h_decomps[nd];
+      memset(&d, 0, sizeof(d));
+      d.src = r.d_src;
+      d.in_len = r.src_len;
+      d.dst = r.d_dst;
+      d.cap = r.dst_cap;
+      d.st = s.d_states + i;
+      d.T = reinterpret_cast<DecTables*>(reinterpret_cast<uint8_t*>(s.d_dec) +
+                                         (uint64_t)nd * batch_dec_tables_bytes());
+      d.out_len = s.d_lens + i;
+      d.lut_bits = kLutMaxBits;
+      d.req = i;
+      ++nd;
+    }
+  }
+  ctl.ncomp = nc;
+  ctl.ndecomp = nd;
+  ctl.hist_units = hist_units;
+  ctl.tiles = tile_base;
+  *s.h_ctl = ctl;
+  if (cudaGraphLaunch(s.graph, s.stream) != cudaSuccess ||
+      cudaEventRecord(s.done, s.stream) != cudaSuccess) {
+    cudaGetLastError();
+    return HZ_ERR_CUDA;
+  }
+  s.job = j;
+  j->slot = slot_index;
   return HZ_OK;
 }
 
-// Launch queued batches, in order, while they fit the budget.
-static void admit(BatchState* b) {
+static void finish_job(BatchState* b, Job* j) {
+  const uint32_t n = (uint32_t)j->reqs.size();
+  j->status.assign(n, j->launch_status);
+  j->lens.assign(n, 0);
+  if (j->launch_status == HZ_OK && n) {
+    if (j->plain) {
+      std::vector<int32_t> s(n);
+      if (cudaMemcpy(s.data(), j->d_status, n * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+              cudaSuccess ||
+          cudaMemcpy(j->lens.data(), j->d_lens, n * sizeof(uint64_t), cudaMemcpyDeviceToHost) !=
+              cudaSuccess) {
+        j->status.assign(n, HZ_ERR_CUDA);
+      } else {
+        for (uint32_t i = 0; i < n; ++i) j->status[i] = s[i];
+      }
+    } else {
+      const Slot& s = b->slots[j->slot];
+      for (uint32_t i = 0; i < n; ++i) {
+        const BatchResult& r = s.h_results[i];
+        if (r.req < n) {
+          j->status[r.req] = r.status;
+          j->lens[r.req] = r.out_len;
+        }
+      }
+    }
+  }
+  if (j->slot >= 0) b->slots[j->slot].job = nullptr;
+  b->admitted -= j->footprint;
+  j->done = true;
+}
+
+// Retire finished batches, then launch queued ones, in order, while slots and
+// the budget allow.
+static void progress(BatchState* b) {
+  for (Job* j : b->queue) {
+    if (!j->launched || j->done) continue;
+    cudaEvent_t ev = j->plain ? j->plain_done : b->slots[j->slot].done;
+    if (j->launch_status != HZ_OK || cudaEventQuery(ev) == cudaSuccess) finish_job(b, j);
+    else cudaGetLastError();
+  }
+  while (!b->queue.empty() && b->queue.front()->done) b->queue.pop_front();
   for (Job* j : b->queue) {
     if (j->launched) continue;
     if (b->budget && b->admitted + j->footprint > b->budget) break;
-    j->launch_status = launch_job(b, j);
-    if (j->launch_status != HZ_OK) {
-      j->launched = true;
-      cudaEventRecord(j->done, b->stream);
+    if (j->plain) {
+      // plain batches run one at a time, in order, on their own stream
+      j->launch_status = launch_plain(b, j);
+    } else {
+      int free_slot = -1;
+      for (int k = 0; k < kSlots; ++k)
+        if (!b->slots[k].job) {
+          free_slot = k;
+          break;
+        }
+      if (free_slot < 0) break;
+      j->launch_status = launch_batched(b, j, free_slot);
+      if (j->launch_status != HZ_OK) j->slot = -1;
     }
+    j->launched = true;
+    b->admitted += j->footprint;
+    if (j->launch_status != HZ_OK) finish_job(b, j);
   }
 }
 
@@ -124,28 +415,23 @@ hz_status hz_batch_submit(BatchState* b, hz_ctx* ctx, const hz_request* reqs, ui
   for (uint32_t i = 0; i < count; ++i) {
     const hz_request& r = reqs[i];
     if ((r.op != HZ_OP_COMPRESS && r.op != HZ_OP_DECOMPRESS) || !r.d_dst || !r.d_src ||
-        r.src_len > 0xFFFFFFFFull || r.block_size > hz::kMaxBlock)
+        r.src_len > 0xFFFFFFFFull || r.block_size > kMaxBlock || ((uintptr_t)r.d_dst & 3) ||
+        (r.op == HZ_OP_DECOMPRESS && ((uintptr_t)r.d_src & 3)))
       return HZ_ERR_ARG;
     fp += r.src_len + r.dst_cap;
   }
-  if (b->budget && fp > b->budget) return HZ_ERR_BUSY;
   Job* j = new Job();
-  j->ticket = b->next_ticket++;
   j->reqs.assign(reqs, reqs + count);
-  j->footprint = fp;
-  const uint32_t m = count ? count : 1;
-  if (cudaMalloc(&j->d_status, m * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&j->d_lens, m * sizeof(uint64_t)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    free_job(j);
-    return HZ_ERR_NOMEM;
+  j->plain = b->plain;
+  j->footprint = fp + (j->plain ? 0 : scratch_bytes(j->reqs));
+  if (b->budget && j->footprint > b->budget) {
+    delete j;
+    return HZ_ERR_BUSY;
   }
-  cudaMemsetAsync(j->d_status, 0, m * sizeof(int32_t), b->stream);
-  cudaMemsetAsync(j->d_lens, 0, m * sizeof(uint64_t), b->stream);
+  j->ticket = b->next_ticket++;
   b->queue.push_back(j);
   b->jobs[j->ticket] = j;
-  admit(b);
+  progress(b);
   *ticket = j->ticket;
   return HZ_OK;
 }
@@ -157,44 +443,20 @@ hz_status hz_batch_poll(BatchState* b, uint64_t ticket, int64_t timeout_ns, hz_s
   Job* j = it->second;
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
-    // retire finished batches at the head so that waiting ones can be admitted
-    while (!b->queue.empty() && b->queue.front()->launched &&
-           cudaEventQuery(b->queue.front()->done) == cudaSuccess) {
-      Job* h = b->queue.front();
-      b->queue.pop_front();
-      b->admitted -= h->launch_status == HZ_OK ? h->footprint : 0;
-      h->footprint = 0;
-    }
-    admit(b);
-    if (j->launched && cudaEventQuery(j->done) == cudaSuccess) break;
-    cudaGetLastError();
+    progress(b);
+    if (j->done) break;
     if (timeout_ns == 0) return HZ_PENDING;
     if (timeout_ns > 0 && std::chrono::duration_cast<std::chrono::nanoseconds>(
                               std::chrono::steady_clock::now() - t0)
                                   .count() >= timeout_ns)
       return HZ_PENDING;
-    std::this_thread::sleep_for(std::chrono::microseconds(20));
+    std::this_thread::sleep_for(std::chrono::microseconds(10));
   }
   const uint32_t n = (uint32_t)j->reqs.size();
-  hz_status rs = j->launch_status;
-  if (rs == HZ_OK && n) {
-    std::vector<int32_t> s(n);
-    std::vector<uint64_t> l(n);
-    if (cudaMemcpy(s.data(), j->d_status, n * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
-            cudaSuccess ||
-        cudaMemcpy(l.data(), j->d_lens, n * sizeof(uint64_t), cudaMemcpyDeviceToHost) !=
-            cudaSuccess)
-      rs = HZ_ERR_CUDA;
-    for (uint32_t i = 0; i < n && rs == HZ_OK; ++i) {
-      if (per_req) per_req[i] = s[i];
-      if (out_lens) out_lens[i] = l[i];
-    }
+  for (uint32_t i = 0; i < n; ++i) {
+    if (per_req) per_req[i] = j->status[i];
+    if (out_lens) out_lens[i] = j->lens[i];
   }
-  if (rs != HZ_OK)
-    for (uint32_t i = 0; i < n; ++i) {
-      if (per_req) per_req[i] = rs;
-      if (out_lens) out_lens[i] = 0;
-    }
   b->jobs.erase(it);
   free_job(j);
   return HZ_OK;

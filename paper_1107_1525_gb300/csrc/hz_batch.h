@@ -12,5 +12,8 @@ hz_status hz_batch_submit(BatchState* b, hz_ctx* ctx, const hz_request* reqs, ui
                           uint64_t* ticket);
 hz_status hz_batch_poll(BatchState* b, uint64_t ticket, int64_t timeout_ns, hz_status* per_req,
                         uint64_t* out_lens);
-// Block size used when a caller passes 0, by input size class.
+// Block size used when a caller passes 0 and nothing has been tuned.
 uint32_t hz_batch_tuned_block_size(uint64_t n);
+// Plain mode: requests run one after another through hz_compress / hz_decompress.
+void hz_batch_set_plain(BatchState* b, bool plain);
+bool hz_batch_plain(BatchState* b);

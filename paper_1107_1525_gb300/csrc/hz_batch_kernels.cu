@@ -1,0 +1,306 @@
+// hz_batch_kernels.cu -- kernels of the batched path (hz_submit / hz_poll).
+//
+// A batch holds any mix of compress and decompress requests over independent
+// buffers of uneven sizes.  Each phase of the method runs as one persistent
+// kernel over the whole batch: CTAs take work units from a ticket counter over
+// a flattened (request, unit) index -- 64 KiB histogram chunks, 8192-symbol
+// encoder tiles, groups of decoder blocks -- and find the request a unit
+// belongs to by binary search over per-request unit prefixes.  Phases that
+// need a whole request (code construction, the tile scan, decode set-up) run
+// one CTA per request in a grid-stride loop.  Every launch has a fixed grid
+// and reads the batch's sizes from device memory, so the host captures the
+// sequence once in a CUDA graph and replays it for every batch.
+#include <stddef.h>
+
+#include "hz_batch_dev.h"
+#include "hz_build_dev.cuh"
+#include "hz_decode_dev.cuh"
+#include "hz_encode_dev.cuh"
+#include "hz_hist_dev.cuh"
+
+namespace hz {
+
+// Index of the request whose [base, base + units) range holds unit u.
+template <class Item, class BaseF>
+__device__ __forceinline__ uint32_t find_item(const Item* items, uint32_t count, uint32_t u,
+                                              BaseF base) {
+  uint32_t lo = 0, hi = count;  // first item with base > u, minus one
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (base(items[mid]) <= u) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ EncodeArgs comp_args(const BatchComp& c) {
+  EncodeArgs a;
+  a.in = c.src;
+  a.n = c.n;
+  a.B = c.B;
+  a.nb = c.nb;
+  a.flags = c.flags;
+  a.out = c.dst;
+  a.out_cap = c.cap;
+  a.out_len = c.out_len;
+  a.st = c.st;
+  a.tiles = c.tiles;
+  a.ntiles = c.ntiles;
+  a.fdB = c.fdB;
+  return a;
+}
+
+__device__ __forceinline__ DecodeArgs decomp_args(const BatchDecomp& d) {
+  DecodeArgs a;
+  a.in = d.src;
+  a.in_len = d.in_len;
+  a.out = d.dst;
+  a.out_cap = d.cap;
+  a.out_len = d.out_len;
+  a.st = d.st;
+  a.chase_index = nullptr;  // batched streams must carry the block-offset index
+  a.chase_cap = 0;
+  a.lut_bits = (int)d.lut_bits;
+  return a;
+}
+
+__device__ __forceinline__ uint32_t take_ticket(uint32_t* counter, uint32_t* s_slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) *s_slot = atomicAdd(counter, 1u);
+  __syncthreads();
+  return *s_slot;
+}
+
+// ------------------------------------------------------------- histogram
+__global__ void __launch_bounds__(kHistThreads) batch_hist_kernel(BatchCtl* ctl,
+                                                                   const BatchComp* comps) {
+  __shared__ uint32_t h[256 * 32];
+  __shared__ uint32_t s_u;
+  const uint32_t nunits = ctl->hist_units, ncomp = ctl->ncomp;
+  for (;;) {
+    const uint32_t u = take_ticket(&ctl->tickets[kTicketHist], &s_u);
+    if (u >= nunits) break;
+    const uint32_t i = find_item(comps, ncomp, u, [](const BatchComp& c) { return c.hist_base; });
+    const BatchComp& c = comps[i];
+    const uint64_t lo = (uint64_t)(u - c.hist_base) * kBatchHistChunk;
+    const uint64_t len = c.n - lo < kBatchHistChunk ? c.n - lo : kBatchHistChunk;
+    for (int k = threadIdx.x; k < 256 * 32; k += blockDim.x) h[k] = 0;
+    __syncthreads();
+    count_range(c.src + lo, len, h);
+    __syncthreads();
+    fold_columns(h, c.st->hist);
+  }
+}
+
+// ------------------------------------------------------------- code build
+__global__ void __launch_bounds__(256) batch_build_kernel(BatchCtl* ctl, const BatchComp* comps) {
+  const LenParam none{};
+  for (uint32_t i = blockIdx.x; i < ctl->ncomp; i += gridDim.x) {
+    const BatchComp& c = comps[i];
+    build_codes_device(c.st, 1, none, c.n, c.B, c.nb, c.flags, c.dst, c.cap, c.out_len);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- tile summaries
+__global__ void __launch_bounds__(kEncThreads) batch_summary_kernel(BatchCtl* ctl,
+                                                                    const BatchComp* comps) {
+  __shared__ uint8_t s_len[256];
+  __shared__ uint32_t s_wsum[kEncThreads / 32];
+  __shared__ Summary s_warp[kEncThreads / 32];
+  __shared__ uint32_t s_u;
+  const uint32_t ntiles = ctl->tiles, ncomp = ctl->ncomp;
+  uint32_t cur = 0xFFFFFFFFu;
+  for (;;) {
+    const uint32_t u = take_ticket(&ctl->tickets[kTicketSummary], &s_u);
+    if (u >= ntiles) break;
+    const uint32_t i = find_item(comps, ncomp, u, [](const BatchComp& c) { return c.tile_base; });
+    const BatchComp& c = comps[i];
+    if (c.st->codes.maxlen > (uint32_t)kMaxLen) continue;  // code construction failed
+    if (i != cur) {
+      for (int s = threadIdx.x; s < 256; s += kEncThreads) s_len[s] = c.st->codes.len[s];
+      cur = i;
+      __syncthreads();
+    }
+    bool bad = false;
+    summary_tile(comp_args(c), u - c.tile_base, s_len, s_wsum, s_warp, bad);
+    if (bad) set_error(c.st, HZ_ERR_ARG, 0x200);
+  }
+}
+
+// ------------------------------------------------------------- tile scan
+__global__ void __launch_bounds__(kScanThreads) batch_scan_kernel(BatchCtl* ctl,
+                                                                   const BatchComp* comps) {
+  __shared__ Summary s_warp[kScanThreads / 32];
+  __shared__ ScanState s_carry;
+  for (uint32_t i = blockIdx.x; i < ctl->ncomp; i += gridDim.x) {
+    const BatchComp& c = comps[i];
+    if (c.ntiles == 0 || c.st->codes.maxlen > (uint32_t)kMaxLen) continue;  // uniform
+    scan_tiles_cta(comp_args(c), s_warp, &s_carry);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- packing
+__global__ void __launch_bounds__(kEncThreads, 3) batch_pack_kernel(BatchCtl* ctl,
+                                                                    const BatchComp* comps) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  PackShared& sh = *reinterpret_cast<PackShared*>(smem_raw);
+  __shared__ uint32_t s_u;
+  const uint32_t ntiles = ctl->tiles, ncomp = ctl->ncomp;
+  uint32_t cur = 0xFFFFFFFFu, maxlen = 0;
+  for (;;) {
+    const uint32_t u = take_ticket(&ctl->tickets[kTicketPack], &s_u);
+    if (u >= ntiles) break;
+    const uint32_t i = find_item(comps, ncomp, u, [](const BatchComp& c) { return c.tile_base; });
+    const BatchComp& c = comps[i];
+    if (!c.st->enc_ok || c.st->error) continue;  // uniform: nothing to pack for this request
+    if (i != cur) {
+      pack_load_tables(sh, comp_args(c));
+      maxlen = c.st->codes.maxlen;
+      cur = i;
+      __syncthreads();
+    }
+    pack_one_tile(sh, u - c.tile_base, maxlen);
+  }
+}
+
+// ------------------------------------------------------------- decode set-up
+__global__ void __launch_bounds__(256) batch_dsetup_kernel(BatchCtl* ctl, BatchDecomp* decomps) {
+  for (uint32_t i = blockIdx.x; i < ctl->ndecomp; i += gridDim.x) {
+    BatchDecomp& d = decomps[i];
+    decode_setup_device(decomp_args(d), d.T);
+    __syncthreads();
+  }
+}
+
+// Decode units per stream: groups of 8 warps x `per_warp` blocks, sized so a
+// unit holds at least 256 KiB of output (small blocks share a table load).
+__global__ void __launch_bounds__(1024) batch_dscan_kernel(BatchCtl* ctl, BatchDecomp* decomps) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_carry;
+  const uint32_t n = ctl->ndecomp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  for (uint32_t base = 0; base < n; base += blockDim.x) {
+    __syncthreads();
+    const uint32_t i = base + threadIdx.x;
+    uint32_t units = 0;
+    if (i < n) {
+      BatchDecomp& d = decomps[i];
+      const DecTables* T = d.T;
+      if (T->ok && T->nb) {
+        const uint32_t per_warp = T->B >= (32u << 10) ? 1u : (32u << 10) / T->B;
+        d.per_warp = per_warp;
+        units = (T->nb + 8 * per_warp - 1) / (8 * per_warp);
+      }
+    }
+    uint32_t inc = units;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, dd);
+      if (lane >= dd) inc += o;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0, tot = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      wpre += w < warp ? s_warp[w] : 0u;
+      tot += s_warp[w];
+    }
+    const uint32_t carry = s_carry;
+    if (i < n) decomps[i].unit_base = carry + wpre + inc - units;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + tot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ctl->dec_units = s_carry;
+}
+
+// ------------------------------------------------------------- block decoding
+__global__ void __launch_bounds__(kFastThreads) batch_decode_kernel(BatchCtl* ctl,
+                                                                    const BatchDecomp* decomps) {
+  __shared__ FastShared sh;
+  __shared__ uint32_t s_u;
+  const uint32_t nunits = ctl->dec_units, n = ctl->ndecomp;
+  uint32_t cur = 0xFFFFFFFFu;
+  bool simple = false;
+  for (;;) {
+    const uint32_t u = take_ticket(&ctl->tickets[kTicketDecode], &s_u);
+    if (u >= nunits) break;
+    const uint32_t i = find_item(decomps, n, u, [](const BatchDecomp& d) { return d.unit_base; });
+    const BatchDecomp& d = decomps[i];
+    const DecTables* T = d.T;
+    if (i != cur) {
+      const int W = (int)T->lut_bits;
+      for (int k = threadIdx.x; k < (1 << W); k += kFastThreads) sh.lut[k] = T->lut[k];
+      load_canon(sh.c, T, threadIdx.x, kFastThreads);
+      cur = i;
+      __syncthreads();
+      simple = T->complete && sh.c.maxlen <= sh.c.W;
+    }
+    const DecodeArgs a = decomp_args(d);
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t k0 = ((u - d.unit_base) * 8 + warp) * d.per_warp;
+    for (uint32_t j = 0; j < d.per_warp; ++j) {
+      const uint32_t k = k0 + j;
+      if (k >= sh.c.nb) break;
+      if (simple) decode_block_warp<true>(a, sh, k);
+      else decode_block_warp<false>(a, sh, k);
+    }
+  }
+}
+
+// ------------------------------------------------------------- results
+__global__ void batch_finish_kernel(BatchCtl* ctl, const BatchComp* comps,
+                                    const BatchDecomp* decomps, BatchResult* results) {
+  const uint32_t nc = ctl->ncomp, nd = ctl->ndecomp;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc + nd;
+       i += gridDim.x * blockDim.x) {
+    const bool is_c = i < nc;
+    DevState* st = is_c ? comps[i].st : decomps[i - nc].st;
+    const uint64_t* len = is_c ? comps[i].out_len : decomps[i - nc].out_len;
+    BatchResult r;
+    r.req = is_c ? comps[i].req : decomps[i - nc].req;
+    r.status = -(int32_t)st->error;
+    r.out_len = *len;
+    results[i] = r;
+  }
+}
+
+// ------------------------------------------------------------- per-request state
+// Clear what must start at zero in every request's state: status words,
+// counters, histogram, scan flags (everything before the code table).
+__global__ void batch_clear_kernel(BatchCtl* ctl, const BatchComp* comps,
+                                   const BatchDecomp* decomps) {
+  constexpr uint32_t kWords = (uint32_t)(offsetof(DevState, codes) / 4);
+  const uint32_t nc = ctl->ncomp, nd = ctl->ndecomp;
+  for (uint32_t i = blockIdx.x; i < nc + nd; i += gridDim.x) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(i < nc ? comps[i].st : decomps[i - nc].st);
+    for (uint32_t k = threadIdx.x; k < kWords; k += blockDim.x) w[k] = 0;
+  }
+}
+
+// ------------------------------------------------------------- launch sequence
+void batch_configure() {
+  cudaFuncSetAttribute(batch_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(PackShared));
+}
+
+void batch_enqueue(const BatchLaunch& L, cudaStream_t s) {
+  const int sms = L.num_sms;
+  batch_clear_kernel<<<sms * 2, 256, 0, s>>>(L.ctl, L.comps, L.decomps);
+  batch_hist_kernel<<<sms * kHistCtasPerSm, kHistThreads, 0, s>>>(L.ctl, L.comps);
+  batch_build_kernel<<<sms * 2, 256, 0, s>>>(L.ctl, L.comps);
+  batch_summary_kernel<<<sms * 6, kEncThreads, 0, s>>>(L.ctl, L.comps);
+  batch_scan_kernel<<<sms * 2, kScanThreads, 0, s>>>(L.ctl, L.comps);
+  batch_pack_kernel<<<sms * 3, kEncThreads, (int)sizeof(PackShared), s>>>(L.ctl, L.comps);
+  batch_dsetup_kernel<<<sms * 2, 256, 0, s>>>(L.ctl, L.decomps);
+  batch_dscan_kernel<<<1, 1024, 0, s>>>(L.ctl, L.decomps);
+  batch_decode_kernel<<<sms * 4, kFastThreads, 0, s>>>(L.ctl, L.decomps);
+  batch_finish_kernel<<<sms, 256, 0, s>>>(L.ctl, L.comps, L.decomps, L.results);
+}
+
+size_t batch_dec_tables_bytes() { return sizeof(DecTables); }
+
+}  // namespace hz

@@ -30,618 +30,14 @@
 // hide each other's table and load latency.  decode_generic_kernel decodes
 // larger blocks with a whole CTA per block, straight from and to global
 // memory.
-#include "hz_internal.cuh"
+#include "hz_decode_dev.cuh"
 
 namespace hz {
 
-// Lookup-table entry for the W-bit value v (u32):
-//   bits  0..7   first symbol            bits  8..15  second symbol
-//   bits 16..17  symbols resolved (0: the first code is longer than W bits,
-//                or no code matches), 1 or 2
-//   bits 18..22  bits consumed by them   bits 23..26  length of the first code
-__host__ __device__ constexpr uint32_t lut_entry(uint32_t s0, uint32_t s1, uint32_t ns,
-                                                 uint32_t nbits, uint32_t l0) {
-  return s0 | (s1 << 8) | (ns << 16) | (nbits << 18) | (l0 << 23);
-}
-__device__ __forceinline__ uint32_t e_ns(uint32_t e) { return (e >> 16) & 3u; }
-__device__ __forceinline__ uint32_t e_nbits(uint32_t e) { return (e >> 18) & 31u; }
-__device__ __forceinline__ uint32_t e_l0(uint32_t e) { return (e >> 23) & 15u; }
-
-struct DecTables {
-  uint32_t ok;          // 1 once the header has been checked
-  uint32_t flags, B, nb;
-  uint64_t n;
-  uint64_t blocks_at;   // byte offset of the record area
-  uint32_t maxlen, lut_bits;
-  uint32_t complete;            // Kraft sum exactly 1: every bit string decodes
-  uint32_t cnt[kMaxLen + 1];
-  uint32_t offs[kMaxLen + 1];   // position in sorted[] of the first code of each length
-  uint64_t first[kMaxLen + 1];  // first canonical code of each length
-  uint8_t sorted[256];          // symbols in (length, byte) order
-  uint32_t lut[1 << kLutMaxBits];
-};
-
 size_t dec_tables_bytes() { return sizeof(DecTables); }
 
-__device__ __forceinline__ uint32_t ld_u32_bytes(const uint8_t* p) {
-  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
-}
-
-// ================================================================ setup
 __global__ void __launch_bounds__(256) decode_setup_kernel(DecodeArgs a, DecTables* T) {
-  __shared__ uint32_t s_len[256];
-  __shared__ uint8_t s_sorted[256];
-  __shared__ uint32_t cnt[kMaxLen + 1];
-  __shared__ uint64_t first[kMaxLen + 1];
-  __shared__ uint32_t offs[kMaxLen + 1];
-  __shared__ int s_ok;
-  __shared__ uint32_t s_maxlen;
-  const int t = threadIdx.x;
-  if (t == 0) {
-    T->ok = 0;
-    a.st->dec_deferred = 0;
-    s_ok = a.in_len >= kHeaderBytes;
-  }
-  if (t <= kMaxLen) cnt[t] = 0;
-  __syncthreads();
-  if (!s_ok) {
-    if (t == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x300);
-    return;  // uniform: every thread leaves here
-  }
-  const uint8_t* h = a.in;
-  const uint32_t flags = ld_u32_bytes(h + 4);
-  const uint64_t n = (uint64_t)ld_u32_bytes(h + 8) | ((uint64_t)ld_u32_bytes(h + 12) << 32);
-  const uint32_t B = ld_u32_bytes(h + 16);
-  const uint32_t nb = ld_u32_bytes(h + 20);
-  bool ok = h[0] == 'H' && h[1] == 'Z' && h[2] == 'B' && h[3] == '1';
-  ok = ok && (flags & ~kFlagIndex) == 0 && B >= 1 && B <= kMaxBlock && n <= 0xFFFFFFFFull;
-  ok = ok && (uint64_t)nb == (n + B - 1) / (B ? B : 1);
-  const uint64_t blocks_at = kHeaderBytes + ((flags & kFlagIndex) ? 4ull * nb : 0ull);
-  ok = ok && blocks_at <= a.in_len;
-  const uint32_t l = h[24 + t];
-  s_len[t] = l;
-  if (l > (uint32_t)kMaxLen) ok = false;
-  if (!ok) s_ok = 0;
-  __syncthreads();
-  if (s_ok && l) atomicAdd(&cnt[l], 1u);
-  __syncthreads();
-  if (t == 0 && s_ok) {
-    // Kraft's inequality exactly: sum cnt[k] * 2^(64-k) <= 2^64
-    uint64_t lo = 0, hi = 0, code = 0;
-    uint32_t maxl = 0, nsym = 0, off = 0;
-    first[0] = 0;
-    offs[0] = 0;
-    for (int k = 1; k <= kMaxLen; ++k) {
-      const uint64_t c = cnt[k];
-      const uint64_t add_hi = k < 64 ? (c >> k) : 0;
-      const uint64_t add_lo = k < 64 ? (c << (64 - k)) : c;
-      const uint64_t prev = lo;
-      lo += add_lo;
-      hi += add_hi + (lo < prev ? 1 : 0);
-      code = (code + cnt[k - 1]) << 1;
-      first[k] = code;
-      offs[k] = off;
-      off += (uint32_t)c;
-      if (c) {
-        maxl = k;
-        nsym += (uint32_t)c;
-      }
-    }
-    const bool kraft = hi == 0 || (hi == 1 && lo == 0);
-    if (!kraft || (n > 0 && nsym == 0)) s_ok = 0;
-    s_maxlen = maxl;
-    T->complete = hi == 1 && lo == 0;
-  }
-  __syncthreads();
-  if (!s_ok) {
-    if (t == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x301);
-    return;  // uniform
-  }
-  // symbols in (length, byte) order
-  if (l) {
-    uint32_t rank = 0;
-    for (int u = 0; u < t; ++u) rank += s_len[u] == l;
-    s_sorted[offs[l] + rank] = (uint8_t)t;
-  }
-  __syncthreads();
-  T->sorted[t] = s_sorted[t];
-  if (t <= kMaxLen) {
-    T->cnt[t] = cnt[t];
-    T->offs[t] = offs[t];
-    T->first[t] = first[t];
-  }
-  // lookup table: the code that prefixes the W-bit value v, and the next one
-  // when it also fits in the W bits
-  const int W = a.lut_bits;
-  const uint32_t maxl = s_maxlen;
-  auto code_at = [&](uint32_t v, int width, uint32_t& sym) -> uint32_t {
-    for (int k = 1; k <= width && k <= (int)maxl; ++k) {
-      if (!cnt[k]) continue;
-      const uint64_t p = v >> (width - k);
-      if (p >= first[k] && p - first[k] < cnt[k]) {
-        sym = s_sorted[offs[k] + (uint32_t)(p - first[k])];
-        return (uint32_t)k;
-      }
-    }
-    return 0;
-  };
-  for (uint32_t v = t; v < (1u << W); v += blockDim.x) {
-    uint32_t s0 = 0, s1 = 0;
-    const uint32_t l0 = code_at(v, W, s0);
-    uint32_t e = 0;
-    if (l0) {
-      const uint32_t rest = W - l0;
-      const uint32_t l1 = rest ? code_at(v & ((1u << rest) - 1u), (int)rest, s1) : 0u;
-      e = l1 ? lut_entry(s0, s1, 2, l0 + l1, l0) : lut_entry(s0, 0, 1, l0, l0);
-    }
-    T->lut[v] = e;
-  }
-  const bool cap_ok = n <= a.out_cap;
-  if (t == 0) {
-    T->flags = flags;
-    T->B = B;
-    T->nb = nb;
-    T->n = n;
-    T->blocks_at = blocks_at;
-    T->maxlen = maxl;
-    T->lut_bits = (uint32_t)W;
-    *a.out_len = n;
-    if (!cap_ok) set_error(a.st, HZ_ERR_CAPACITY, 0x302);
-    // blocks too large for the fast kernel all go to the generic one
-    if (B > 65536) a.st->dec_deferred = nb;
-  }
-  if (!cap_ok) return;  // uniform
-  __syncthreads();
-  if (t == 0) {
-    bool chase_ok = true;
-    if (!(flags & kFlagIndex)) {
-      // no stored index: walk the delimiters (one dependent load per block)
-      if (nb > a.chase_cap) {
-        set_error(a.st, HZ_ERR_NOMEM, 0x303);
-        chase_ok = false;
-      }
-      uint64_t O = 0;
-      for (uint32_t k = 0; chase_ok && k < nb; ++k) {
-        const uint64_t at = blocks_at + 4 * O;
-        if (at + 4 > a.in_len || O > 0xFFFFFFFFull) {
-          set_error(a.st, HZ_ERR_CORRUPT, 0x304);
-          chase_ok = false;
-          break;
-        }
-        a.chase_index[k] = (uint32_t)O;
-        O += 1 + ceil32(*reinterpret_cast<const uint32_t*>(a.in + at));
-      }
-    }
-    if (chase_ok) {
-      __threadfence();
-      T->ok = 1;
-    }
-  }
-}
-
-// ================================================================ shared pieces
-struct CanonTables {
-  uint32_t cnt[kMaxLen + 1];
-  uint32_t offs[kMaxLen + 1];
-  uint64_t first[kMaxLen + 1];
-  uint8_t sorted[256];
-  uint32_t maxlen, W, flags, B, nb;
-  uint64_t n, blocks_at;
-};
-
-__device__ __forceinline__ void load_canon(CanonTables& c, const DecTables* T, int tid, int nt) {
-  for (int i = tid; i <= kMaxLen; i += nt) {
-    c.cnt[i] = T->cnt[i];
-    c.offs[i] = T->offs[i];
-    c.first[i] = T->first[i];
-  }
-  for (int i = tid; i < 256; i += nt) c.sorted[i] = T->sorted[i];
-  if (tid == 0) {
-    c.maxlen = T->maxlen;
-    c.W = T->lut_bits;
-    c.flags = T->flags;
-    c.B = T->B;
-    c.nb = T->nb;
-    c.n = T->n;
-    c.blocks_at = T->blocks_at;
-  }
-}
-
-// A code longer than W bits at the top of v64 (canonical first-code search):
-// returns length << 8 | symbol, 0 when nothing matches.  (Results come back
-// packed, never through a reference, so callers keep them in registers.)
-__device__ __noinline__ uint32_t decode_long(const CanonTables& c, uint64_t v64) {
-  for (uint32_t k = c.W + 1; k <= c.maxlen; ++k) {
-    const uint32_t n = c.cnt[k];
-    if (!n) continue;
-    const uint64_t p = v64 >> (64 - k);
-    if (p >= c.first[k] && p - c.first[k] < n)
-      return (k << 8) | c.sorted[c.offs[k] + (uint32_t)(p - c.first[k])];
-  }
-  return 0;
-}
-
-// Record k: check it and return its payload position.  Shared by both kernels.
-struct RecInfo {
-  uint64_t rec;
-  uint32_t bits, nw, cnt_k;
-  bool ok;
-};
-
-__device__ __forceinline__ RecInfo read_record(const DecodeArgs& a, const CanonTables& c,
-                                               uint32_t k) {
-  RecInfo r;
-  const uint32_t* idx = (c.flags & kFlagIndex)
-                            ? reinterpret_cast<const uint32_t*>(a.in + kHeaderBytes)
-                            : a.chase_index;
-  const uint64_t O = idx[k];
-  r.rec = c.blocks_at + 4 * O;
-  r.bits = 0;
-  r.nw = 0;
-  bool ok = r.rec + 4 <= a.in_len;
-  if (ok) {
-    r.bits = *reinterpret_cast<const uint32_t*>(a.in + r.rec);
-    r.nw = ceil32(r.bits);
-    ok = r.rec + 4 + 4ull * r.nw <= a.in_len;
-  }
-  if (ok) {
-    if (k + 1 < c.nb) ok = (uint64_t)idx[k + 1] == O + 1 + r.nw;
-    else ok = r.rec + 4 + 4ull * r.nw == a.in_len;
-  }
-  const uint64_t lo = (uint64_t)k * c.B;
-  r.cnt_k = (uint32_t)((lo + c.B <= c.n) ? c.B : c.n - lo);
-  // at least one bit per symbol, at most maxlen bits per symbol
-  ok = ok && r.bits >= r.cnt_k && (uint64_t)r.bits <= (uint64_t)r.cnt_k * c.maxlen;
-  if (ok && (r.bits & 31)) {
-    // padding bits after the last code must be zero
-    const uint32_t last = *reinterpret_cast<const uint32_t*>(a.in + r.rec + 4 + 4ull * (r.nw - 1));
-    ok = (last & ((1u << (32 - (r.bits & 31))) - 1u)) == 0;
-  }
-  r.ok = ok;
-  return r;
-}
-
-// ================================================================ fast kernel
-// One warp decodes one block.  Lane i takes the i-th of 32 equal word ranges
-// of the payload; ranges of ~2000 symbols make the resynchronisation (tens of
-// bits) negligible, and every step after the table lookup is warp-local.
-constexpr int kFastThreads = 256;
-constexpr uint32_t kFastMaxB = 65536;  // larger blocks go to the generic kernel
-
-__host__ __device__ __forceinline__ bool fast_block_size(uint32_t B) { return B <= kFastMaxB; }
-
-__device__ __forceinline__ bool fast_capable(uint32_t B, uint32_t nw) {
-  (void)nw;
-  return fast_block_size(B);
-}
-
-// Per lane, a ring of kRingSlots slots of 32 bytes of its payload range in
-// shared memory, fed by cp.async.  Refills happen at warp-uniform points,
-// every kRefillSteps decode steps: each lane keeps the three slots after the
-// one it is reading requested, and makes sure the next one has landed.  A
-// step advances at most W <= 12 bits, so kRefillSteps steps stay within two
-// slots and the window refills in between are plain shared-memory reads.
-constexpr uint32_t kSlotWords = 8;
-constexpr uint32_t kRingSlots = 4;
-constexpr uint32_t kRingWords = kSlotWords * kRingSlots;
-constexpr uint32_t kRingStride = kRingWords + 4;  // words between lanes' rings (16-byte aligned)
-constexpr uint32_t kRefillSteps = 16;
-
-struct FastShared {
-  uint32_t lut[1 << kLutMaxBits];
-  CanonTables c;
-  __align__(16) uint32_t ring[kFastThreads * kRingStride];
-};
-
-__device__ __forceinline__ void cp_async16(uint32_t smem_addr, const void* gptr, uint32_t bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr), "l"(gptr),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// 64-bit window over the payload, refilled from the lane's ring.  Words are
-// indexed from the 16-byte-aligned address at or below the payload start.
-struct RingWin {
-  const uint8_t* abase;  // 16-byte aligned base of the payload's slots
-  uint32_t full_slots;   // slots [0, full_slots) lie wholly inside the stream buffer
-  uint32_t tail_bytes;   // bytes of slot full_slots inside the buffer
-  const uint32_t* ring;  // my ring (generic pointer into shared memory)
-  uint32_t ring_s;       // my ring (shared-memory address)
-  uint32_t off_w;        // payload word 0 = aligned word off_w
-  uint32_t A;            // aligned word index of w0
-  uint32_t next_slot;    // next slot index (absolute) to request
-  uint32_t w0, w1;
-  __device__ __forceinline__ void setup(const uint8_t* payload, const uint8_t* gend,
-                                        const uint32_t* my_ring) {
-    abase = reinterpret_cast<const uint8_t*>(((uintptr_t)payload) & ~(uintptr_t)15);
-    off_w = (uint32_t)(payload - abase) >> 2;
-    const uint64_t span = (uint64_t)(gend - abase);
-    full_slots = (uint32_t)(span >> 5);
-    tail_bytes = (uint32_t)(span & 31);
-    ring = my_ring;
-    ring_s = (uint32_t)__cvta_generic_to_shared(my_ring);
-  }
-  __device__ __forceinline__ void request(uint32_t h) {
-    const uint32_t bytes = h < full_slots ? 32u : (h == full_slots ? tail_bytes : 0u);
-    const uint32_t b0 = bytes < 16 ? bytes : 16u, b1 = bytes > 16 ? bytes - 16 : 0u;
-    const uint8_t* src = abase + 32ull * h;
-    const uint32_t dst = ring_s + 32 * (h % kRingSlots);
-    cp_async16(dst, b0 ? src : abase, b0);
-    cp_async16(dst + 16, b1 ? src + 16 : abase, b1);
-    cp_async_commit();
-  }
-  // start at payload bit `pos` (waits for the first two slots)
-  __device__ __forceinline__ void init(uint32_t pos) {
-    cp_async_wait<0>();
-    A = off_w + (pos >> 5);
-    const uint32_t h0 = A / kSlotWords;
-    request(h0);
-    request(h0 + 1);
-    request(h0 + 2);
-    next_slot = h0 + 3;
-    cp_async_wait<1>();
-    w0 = ring[A % kRingWords];
-    w1 = ring[(A + 1) % kRingWords];
-  }
-  // warp-uniform refill point (see above)
-  __device__ __forceinline__ void refill() {
-    const uint32_t cur = (A + 1) / kSlotWords;
-    while (next_slot <= cur + 3) request(next_slot++);
-    cp_async_wait<2>();
-  }
-  __device__ __forceinline__ uint32_t peek(uint32_t pos) const { return __funnelshift_l(w1, w0, pos); }
-  // after an advance of at most 32 bits
-  __device__ __forceinline__ void cross(uint32_t pos) {
-    if (off_w + (pos >> 5) != A) {
-      ++A;
-      w0 = w1;
-      w1 = ring[(A + 1) % kRingWords];
-    }
-  }
-};
-
-// 64-bit window over the payload words read straight from global memory
-// (through L1), refilled one word at a time: the fix-up's short walks and
-// the rare codes longer than W bits use it.
-struct GWin {
-  const uint32_t* p;
-  uint32_t nw, wi, w0, w1;
-  __device__ __forceinline__ uint32_t ld(uint32_t i) const { return i < nw ? __ldg(p + i) : 0u; }
-  __device__ __forceinline__ void init(uint32_t pos) {
-    wi = pos >> 5;
-    w0 = ld(wi);
-    w1 = ld(wi + 1);
-  }
-  __device__ __forceinline__ uint32_t peek(uint32_t pos) const { return __funnelshift_l(w1, w0, pos); }
-  // after an advance of at most 32 bits
-  __device__ __forceinline__ void step(uint32_t pos) {
-    if ((pos >> 5) != wi) {
-      w0 = w1;
-      w1 = ld(wi + 2);
-      ++wi;
-    }
-  }
-  __device__ __forceinline__ uint64_t peek64(uint32_t pos) const {
-    return ((uint64_t)__funnelshift_l(w1, w0, pos) << 32) | __funnelshift_l(ld(wi + 2), w1, pos);
-  }
-  // 64 bits at any position, straight from memory (for the rare long codes)
-  __device__ __forceinline__ uint64_t peek64_at(uint32_t pos) const {
-    const uint32_t i = pos >> 5;
-    const uint32_t a0 = ld(i), a1 = ld(i + 1), a2 = ld(i + 2);
-    return ((uint64_t)__funnelshift_l(a1, a0, pos) << 32) | __funnelshift_l(a2, a1, pos);
-  }
-};
-
-// One symbol at pos: length << 8 | symbol (0 when no code matches).
-__device__ __forceinline__ uint32_t one_symbol(const FastShared& sh, const GWin& w, uint32_t pos,
-                                               uint32_t W) {
-  const uint32_t e = sh.lut[w.peek(pos) >> (32 - W)];
-  const uint32_t l0 = e_l0(e);
-  if (l0) return (l0 << 8) | (e & 0xFFu);
-  return decode_long(sh.c, w.peek64(pos));
-}
-
-// Decode one symbol, advance, and report a miss (no code) through `bad`.
-__device__ __forceinline__ uint32_t take_symbol(const FastShared& sh, GWin& w, uint32_t& pos,
-                                                uint32_t W, bool& bad) {
-  const uint32_t ls = one_symbol(sh, w, pos, W);
-  const uint32_t l = ls >> 8;
-  bad |= l == 0;
-  const uint32_t adv = l ? l : 1u;
-  pos += adv;
-  if (adv <= 32) w.step(pos);
-  else w.init(pos);
-  return ls & 0xFFu;
-}
-
-// One symbol from the ring window: length << 8 | symbol (0 when no code matches).
-template <bool kSimple>
-__device__ __forceinline__ uint32_t ring_symbol(const FastShared& sh, const RingWin& w,
-                                                uint32_t pos, uint32_t W, const GWin& g) {
-  const uint32_t e = sh.lut[w.peek(pos) >> (32 - W)];
-  const uint32_t l0 = e_l0(e);
-  if (kSimple || l0) return (l0 << 8) | (e & 0xFFu);
-  return decode_long(sh.c, g.peek64_at(pos));
-}
-
-// Decode one symbol and advance.  A long code restarts the window (which
-// waits for the ring) -- never the case for kSimple codes.
-template <bool kSimple>
-__device__ __forceinline__ uint32_t ring_take(const FastShared& sh, RingWin& w, uint32_t& pos,
-                                              uint32_t W, const GWin& g, bool& bad) {
-  const uint32_t ls = ring_symbol<kSimple>(sh, w, pos, W, g);
-  const uint32_t l = ls >> 8;
-  if (kSimple) {
-    pos += l;
-    w.cross(pos);
-  } else {
-    bad |= l == 0;
-    const uint32_t adv = l ? l : 1u;
-    pos += adv;
-    if (adv <= 12) w.cross(pos);
-    else w.init(pos);
-  }
-  return ls & 0xFFu;
-}
-
-template <bool kSimple>
-__device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t k) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t W = sh.c.W;
-  RecInfo r;
-  if (lane == 0) r = read_record(a, sh.c, k);
-  r.rec = __shfl_sync(0xFFFFFFFFu, r.rec, 0);
-  r.bits = __shfl_sync(0xFFFFFFFFu, r.bits, 0);
-  r.nw = __shfl_sync(0xFFFFFFFFu, r.nw, 0);
-  r.cnt_k = __shfl_sync(0xFFFFFFFFu, r.cnt_k, 0);
-  r.ok = __shfl_sync(0xFFFFFFFFu, (int)r.ok, 0);
-  if (!r.ok) {
-    if (lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x320);
-    return;
-  }
-  const uint32_t bits = r.bits, nw = r.nw;
-  const uint8_t* payload = a.in + r.rec + 4;
-  GWin g;  // plain reader: long codes and the fix-up
-  g.p = reinterpret_cast<const uint32_t*>(payload);
-  g.nw = nw;
-  RingWin w;
-  w.setup(payload, a.in + a.in_len, sh.ring + threadIdx.x * kRingStride);
-  const uint32_t Lw = (nw + 31) / 32;
-  const uint32_t L = Lw * 32;
-  const uint32_t nsub = (bits + L - 1) / L;
-  const bool active = lane < nsub;
-  const uint32_t my_start = lane * L;
-  const uint32_t my_end = active ? min(my_start + L, bits) : 0u;
-
-  // ---- pass 1: speculative decode of my range, counting symbols
-  uint32_t start = my_start, exit_ = my_start, count = 0;
-  {
-    uint32_t pos = my_start, c = 0;
-    if (active) w.init(pos);
-    bool dummy = false;
-    while (__any_sync(0xFFFFFFFFu, active && pos + W <= my_end)) {
-      if (active) w.refill();
-#pragma unroll 4
-      for (uint32_t s = 0; s < kRefillSteps; ++s) {
-        if (active && pos + W <= my_end) {
-          const uint32_t e = sh.lut[w.peek(pos) >> (32 - W)];
-          const uint32_t ns = e_ns(e);
-          if (!kSimple && ns == 0) {  // a long code, or no code at all on a wrong path
-            const uint32_t l = decode_long(sh.c, g.peek64_at(pos)) >> 8;
-            pos += l ? l : 1u;
-            ++c;
-            w.init(pos);
-          } else {
-            pos += e_nbits(e);
-            c += ns;
-            w.cross(pos);
-          }
-        }
-      }
-    }
-    if (active) {
-      w.refill();
-      while (pos < my_end) {
-        ring_take<kSimple>(sh, w, pos, W, g, dummy);
-        ++c;
-      }
-      exit_ = pos;
-      count = c;
-    }
-  }
-  // ---- fix-up: restart each range at its left neighbour's exit until all agree
-  for (uint32_t round = 0; round <= 32; ++round) {
-    const uint32_t want = __shfl_up_sync(0xFFFFFFFFu, exit_, 1);
-    const bool mismatch = active && lane > 0 && want != start;
-    if (!__any_sync(0xFFFFFFFFu, mismatch)) break;
-    if (mismatch) {
-      // advance the new (a) and old (b) decodes, the one behind first, until they meet
-      uint32_t pa = want, pb = start, ca = 0, cb = 0;
-      GWin wa = g, wb = g;
-      wa.init(pa);
-      wb.init(pb);
-      bool dummy = false;
-      while (pa != pb && (pa < my_end || pb < my_end)) {
-        if (pa < pb) {
-          take_symbol(sh, wa, pa, W, dummy);
-          ++ca;
-        } else {
-          take_symbol(sh, wb, pb, W, dummy);
-          ++cb;
-        }
-      }
-      if (pa == pb) {
-        count = count - cb + ca;
-      } else {
-        exit_ = pa;
-        count = ca;
-      }
-      start = want;
-    }
-  }
-  // ---- exclusive scan of the counts
-  const uint32_t v = active ? count : 0u;
-  uint32_t inc = v;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
-    if (lane >= (uint32_t)d) inc += o;
-  }
-  const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
-  const uint32_t last_exit = __shfl_sync(0xFFFFFFFFu, exit_, nsub - 1);
-  if (total != r.cnt_k || last_exit != bits) {
-    if (lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x321);
-    cp_async_wait<0>();
-    return;  // uniform
-  }
-  // ---- pass 2: decode from the true boundary and store the symbols
-  bool bad = false;
-  {
-    uint32_t pos = start, rem = active ? v : 0u;
-    uint8_t* dst = a.out + (uint64_t)k * sh.c.B + (inc - v);
-    if (rem) {
-      w.init(pos);
-      // bytes up to a 16-byte boundary (at most 15 steps: within the slots init awaited)
-      while (rem && (((uintptr_t)dst) & 15)) {
-        *dst++ = (uint8_t)ring_take<kSimple>(sh, w, pos, W, g, bad);
-        --rem;
-      }
-    }
-    // 16 symbols per 16-byte store, one refill point per 16 symbols
-    while (__any_sync(0xFFFFFFFFu, rem >= 16)) {
-      if (rem >= 16) {
-        w.refill();
-        uint32_t q[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          uint32_t word = 0;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) word |= ring_take<kSimple>(sh, w, pos, W, g, bad) << (8 * b);
-          q[j] = word;
-        }
-        *reinterpret_cast<uint4*>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
-        dst += 16;
-        rem -= 16;
-      }
-    }
-    if (rem) {
-      w.refill();
-      while (rem) {
-        *dst++ = (uint8_t)ring_take<kSimple>(sh, w, pos, W, g, bad);
-        --rem;
-      }
-    }
-    if (active && v) bad |= pos != exit_;
-  }
-  cp_async_wait<0>();  // nothing of this block may land in the ring after we leave
-  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x322);
+  decode_setup_device(a, T);
 }
 
 __global__ void __launch_bounds__(kFastThreads) decode_fast_kernel(DecodeArgs a,
@@ -660,169 +56,6 @@ __global__ void __launch_bounds__(kFastThreads) decode_fast_kernel(DecodeArgs a,
   for (uint32_t k = blockIdx.x * warps + (threadIdx.x >> 5); k < sh.c.nb; k += stride) {
     if (simple) decode_block_warp<true>(a, sh, k);
     else decode_block_warp<false>(a, sh, k);
-  }
-}
-
-// ================================================================ generic kernel
-struct BitReader {
-  const uint32_t* p;
-  uint32_t nw, wi, w0, w1, w2;
-  __device__ __forceinline__ uint32_t ld(uint32_t i) const { return i < nw ? __ldg(p + i) : 0u; }
-  __device__ __forceinline__ void init(const uint32_t* p_, uint32_t nw_, uint32_t pos) {
-    p = p_;
-    nw = nw_;
-    wi = pos >> 5;
-    w0 = ld(wi);
-    w1 = ld(wi + 1);
-    w2 = ld(wi + 2);
-  }
-  __device__ __forceinline__ void seek(uint32_t pos) {  // forward only
-    while ((pos >> 5) > wi) {
-      w0 = w1;
-      w1 = w2;
-      w2 = ld(wi + 3);
-      ++wi;
-    }
-  }
-  __device__ __forceinline__ uint32_t peek32(uint32_t pos) const {
-    return __funnelshift_l(w1, w0, pos & 31);
-  }
-  __device__ __forceinline__ uint64_t peek64(uint32_t pos) const {
-    const uint32_t s = pos & 31;
-    return ((uint64_t)__funnelshift_l(w1, w0, s) << 32) | __funnelshift_l(w2, w1, s);
-  }
-};
-
-struct GenShared {
-  uint32_t lut[1 << kLutMaxBits];
-  CanonTables c;
-};
-
-__device__ __forceinline__ uint32_t generic_one(const GenShared& sh, const BitReader& br,
-                                                uint32_t pos, uint32_t& sym) {
-  const uint32_t e = sh.lut[br.peek32(pos) >> (32 - sh.c.W)];
-  const uint32_t l0 = e_l0(e);
-  if (l0) {
-    sym = e & 0xFFu;
-    return l0;
-  }
-  const uint32_t ls = decode_long(sh.c, br.peek64(pos));
-  sym = ls & 0xFFu;
-  return ls >> 8;
-}
-
-template <int NT>
-struct GenBlockShared {
-  uint32_t start[NT], exit[NT], count[NT];
-  uint32_t warp_tot[NT / 32];
-  RecInfo r;
-  int ok;
-};
-
-template <int NT>
-__device__ void decode_block_generic(const DecodeArgs& a, const GenShared& sh,
-                                     GenBlockShared<NT>& bs, uint32_t k) {
-  const int t = threadIdx.x;
-  __syncthreads();  // every thread is done with the previous block's shared state
-  if (t == 0) {
-    bs.r = read_record(a, sh.c, k);
-    // corrupt records are reported by the fast kernel unless it never ran
-    bs.ok = bs.r.ok && !fast_capable(sh.c.B, bs.r.nw) ? 1 : 0;
-    if (!bs.r.ok && !fast_block_size(sh.c.B)) set_error(a.st, HZ_ERR_CORRUPT, 0x310);
-  }
-  __syncthreads();
-  if (!bs.ok) return;  // uniform
-  const uint32_t bits = bs.r.bits;
-  const uint32_t* payload = reinterpret_cast<const uint32_t*>(a.in + bs.r.rec + 4);
-  const uint32_t nw = bs.r.nw;
-  uint32_t L = (bits + NT - 1) / NT;
-  L = L < 32 ? 32 : (L + 31) & ~31u;
-  const uint32_t nsub = (bits + L - 1) / L;
-  const bool active = (uint32_t)t < nsub;
-  const uint32_t my_end = active ? min(((uint32_t)t + 1) * L, bits) : 0u;
-
-  if (active) {
-    uint32_t pos = (uint32_t)t * L, c = 0, sym;
-    BitReader br;
-    br.init(payload, nw, pos);
-    while (pos < my_end) {
-      const uint32_t l = generic_one(sh, br, pos, sym);
-      pos += l ? l : 1u;
-      br.seek(pos);
-      ++c;
-    }
-    bs.start[t] = (uint32_t)t * L;
-    bs.exit[t] = pos;
-    bs.count[t] = c;
-  }
-  for (uint32_t round = 0; round <= (uint32_t)NT; ++round) {
-    __syncthreads();
-    const uint32_t want = (active && t > 0) ? bs.exit[t - 1] : 0u;
-    const bool mismatch = active && t > 0 && want != bs.start[t];
-    if (!__syncthreads_or(mismatch)) break;
-    if (mismatch) {
-      uint32_t pa = want, pb = bs.start[t], ca = 0, cb = 0, sym;
-      BitReader ra, rb;
-      ra.init(payload, nw, pa);
-      rb.init(payload, nw, pb);
-      while (pa != pb && (pa < my_end || pb < my_end)) {
-        if (pa < pb) {
-          const uint32_t l = generic_one(sh, ra, pa, sym);
-          pa += l ? l : 1u;
-          ra.seek(pa);
-          ++ca;
-        } else {
-          const uint32_t l = generic_one(sh, rb, pb, sym);
-          pb += l ? l : 1u;
-          rb.seek(pb);
-          ++cb;
-        }
-      }
-      if (pa == pb) {
-        bs.count[t] = bs.count[t] - cb + ca;
-      } else {
-        bs.exit[t] = pa;
-        bs.count[t] = ca;
-      }
-      bs.start[t] = want;
-    }
-  }
-  __syncthreads();
-  const int lane = t & 31, warp = t >> 5;
-  const uint32_t v = active ? bs.count[t] : 0u;
-  uint32_t inc = v;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
-    if (lane >= d) inc += o;
-  }
-  if (lane == 31) bs.warp_tot[warp] = inc;
-  __syncthreads();
-  uint32_t wpre = 0, total = 0;
-  for (int w = 0; w < NT / 32; ++w) {
-    wpre += w < warp ? bs.warp_tot[w] : 0u;
-    total += bs.warp_tot[w];
-  }
-  const uint32_t my_off = wpre + inc - v;
-  const bool bad = (uint32_t)t == nsub - 1 && (total != bs.r.cnt_k || bs.exit[t] != bits);
-  if (__syncthreads_or(bad)) {
-    if (t == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x311);
-    return;  // uniform
-  }
-  if (active && v) {
-    uint32_t pos = bs.start[t], sym;
-    BitReader br;
-    br.init(payload, nw, pos);
-    uint8_t* dst = a.out + (uint64_t)k * sh.c.B + my_off;
-    bool bad2 = false;
-    for (uint32_t j = 0; j < v; ++j) {
-      const uint32_t l = generic_one(sh, br, pos, sym);
-      bad2 |= l == 0;
-      pos += l ? l : 1u;
-      br.seek(pos);
-      dst[j] = (uint8_t)sym;
-    }
-    if (bad2 || pos != bs.exit[t]) set_error(a.st, HZ_ERR_CORRUPT, 0x312);
   }
 }
 

@@ -24,148 +24,10 @@
 // re-derives the earlier tile's last (< 32) bits from the input; the
 // delimiter of a record is written by the tile holding the record's last
 // symbol.  No word is written twice and the output needs no clearing.
-#include "hz_internal.cuh"
+#include "hz_encode_dev.cuh"
 
 namespace hz {
 
-// A run of symbols, seen as a function on the scan state (O, b):
-//   has == 0: the run lies inside one record:  (O, b) -> (O, b + head)
-//   has == 1: the run starts >= 1 record:      (O, b) -> (O + 1 + ceil((b + head)/32) + omega, tail)
-// head = bits before the run's first record start, omega = words of records
-// that start and end inside the run, tail = bits of the run's last record.
-struct Summary {
-  uint32_t has, head, omega, tail;
-};
-
-struct ScanState {
-  uint64_t O;  // word index (in the record area) of the open record's delimiter
-  uint32_t b;  // payload bits already in the open record
-};
-
-__device__ __forceinline__ Summary combine(const Summary& a, const Summary& x) {  // a, then x
-  Summary r;
-  if (!x.has) {
-    r.has = a.has;
-    r.head = a.has ? a.head : a.head + x.head;
-    r.omega = a.omega;
-    r.tail = a.has ? a.tail + x.head : 0;
-  } else if (!a.has) {
-    r.has = 1;
-    r.head = a.head + x.head;
-    r.omega = x.omega;
-    r.tail = x.tail;
-  } else {
-    r.has = 1;
-    r.head = a.head;
-    r.omega = a.omega + 1 + ceil32((uint64_t)a.tail + x.head) + x.omega;
-    r.tail = x.tail;
-  }
-  return r;
-}
-
-__device__ __forceinline__ ScanState apply(const ScanState& s, const Summary& x) {
-  ScanState r;
-  if (!x.has) {
-    r.O = s.O;
-    r.b = s.b + x.head;
-  } else {
-    r.O = s.O + 1 + ceil32((uint64_t)s.b + x.head) + x.omega;
-    r.b = x.tail;
-  }
-  return r;
-}
-
-__device__ __forceinline__ Summary shfl_up_summary(const Summary& v, int d) {
-  Summary r;
-  r.has = __shfl_up_sync(0xFFFFFFFFu, v.has, d);
-  r.head = __shfl_up_sync(0xFFFFFFFFu, v.head, d);
-  r.omega = __shfl_up_sync(0xFFFFFFFFu, v.omega, d);
-  r.tail = __shfl_up_sync(0xFFFFFFFFu, v.tail, d);
-  return r;
-}
-
-__device__ __forceinline__ Summary load_summary(const TileStatus& t) {
-  return Summary{t.has_head >> 31, t.has_head & 0x7FFFFFFFu, t.omega, t.tail};
-}
-
-__device__ __forceinline__ void store_summary(TileStatus& t, const Summary& s) {
-  t.has_head = (s.has << 31) | s.head;
-  t.omega = s.omega;
-  t.tail = s.tail;
-}
-
-// a virtual empty record before the first one: its "next record" is word 0
-__device__ __forceinline__ ScanState init_state() { return ScanState{~0ull, 0u}; }
-
-__device__ __forceinline__ uint32_t sym_of(const uint32_t (&x)[kEncSymPerThread / 4], int i) {
-  return (x[i >> 2] >> (8 * (i & 3))) & 0xFFu;
-}
-
-// The thread's 32 consecutive symbols (fewer at the end of the input).
-__device__ __forceinline__ void load_symbols(const uint8_t* src, int cnt,
-                                             uint32_t (&x)[kEncSymPerThread / 4]) {
-  if (cnt == kEncSymPerThread && (((uintptr_t)src) & 15) == 0) {
-    uint4 v0 = __ldg(reinterpret_cast<const uint4*>(src));
-    uint4 v1 = __ldg(reinterpret_cast<const uint4*>(src) + 1);
-    x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
-    x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
-  } else {
-    // static indices only, so that x stays in registers
-#pragma unroll
-    for (int w = 0; w < kEncSymPerThread / 4; ++w) x[w] = 0;
-#pragma unroll
-    for (int i = 0; i < kEncSymPerThread; ++i)
-      if (i < cnt) x[i >> 2] |= (uint32_t)src[i] << (8 * (i & 3));
-  }
-}
-
-struct TileGeom {
-  uint32_t lo, hi, g0;  // n < 2^32, so every symbol index fits 32 bits
-  int my_cnt;
-  bool starts_record, ends_record, interior_start;
-};
-
-__device__ __forceinline__ TileGeom tile_geom(uint32_t tile, uint32_t n, const FastDiv& fdB) {
-  TileGeom g;
-  g.lo = tile * (uint32_t)kEncTile;
-  g.hi = n - g.lo > (uint32_t)kEncTile ? g.lo + (uint32_t)kEncTile : n;
-  g.g0 = g.lo + threadIdx.x * (uint32_t)kEncSymPerThread;
-  g.my_cnt = g.g0 >= g.hi ? 0 : (int)min(g.hi - g.g0, (uint32_t)kEncSymPerThread);
-  const uint32_t r_lo = fast_mod(g.lo, fdB);
-  g.starts_record = r_lo == 0;
-  g.ends_record = fast_mod(g.hi, fdB) == 0 || g.hi == n;
-  // first record start after lo: lo + (B - r_lo)
-  g.interior_start = (uint64_t)g.lo + (fdB.d - r_lo) < g.hi;
-  return g;
-}
-
-// Segment summary of one thread's symbols; lens() maps a symbol to its length.
-template <class LenF>
-__device__ __forceinline__ Summary thread_summary(const uint32_t (&x)[kEncSymPerThread / 4],
-                                                  int my_cnt, uint32_t g0, const FastDiv& fdB,
-                                                  LenF lens, bool& bad) {
-  const uint32_t r0 = fast_mod(g0, fdB);
-  uint32_t next_start = r0 == 0 ? 0u : fdB.d - r0;
-  Summary s{0, 0, 0, 0};
-#pragma unroll
-  for (int i = 0; i < kEncSymPerThread; ++i) {
-    if (i < my_cnt) {
-      const uint32_t l = lens(sym_of(x, i));
-      bad |= l == 0;
-      if ((uint32_t)i == next_start) {
-        if (s.has) s.omega += 1 + ceil32(s.tail);
-        s.has = 1;
-        s.tail = 0;
-        next_start += fdB.d;
-      }
-      if (s.has) s.tail += l;
-      else s.head += l;
-    }
-  }
-  return s;
-}
-
-// =================================================================== pass 1
 __global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs a) {
   __shared__ uint8_t s_len[256];  // 64 words: random lookups conflict at most 2-way
   __shared__ uint32_t s_wsum[kEncThreads / 32];
@@ -174,61 +36,9 @@ __global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs 
   if (ct->maxlen > (uint32_t)kMaxLen) return;  // code construction failed; already reported
   for (int s = threadIdx.x; s < 256; s += kEncThreads) s_len[s] = ct->len[s];
   __syncthreads();
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   bool bad = false;
-  for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const TileGeom g = tile_geom(tile, (uint32_t)a.n, a.fdB);
-    uint32_t x[kEncSymPerThread / 4];
-    load_symbols(a.in + g.g0, g.my_cnt, x);
-    if (!g.interior_start) {
-      // the tile lies inside one record (which may start at its first symbol)
-      uint32_t bits = 0, minl = 64;
-      if (g.my_cnt == kEncSymPerThread) {
-#pragma unroll
-        for (int i = 0; i < kEncSymPerThread; ++i) {
-          const uint32_t l = s_len[sym_of(x, i)];
-          minl = min(minl, l);
-          bits += l;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < kEncSymPerThread; ++i) {
-          if (i < g.my_cnt) {
-            const uint32_t l = s_len[sym_of(x, i)];
-            minl = min(minl, l);
-            bits += l;
-          }
-        }
-      }
-      bad |= minl == 0;
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, d);
-      if (lane == 0) s_wsum[warp] = bits;
-      __syncthreads();
-      if (tid == 0) {
-        uint32_t total = 0;
-        for (int w = 0; w < kEncThreads / 32; ++w) total += s_wsum[w];
-        store_summary(a.tiles[tile], g.starts_record ? Summary{1, 0, 0, total}
-                                                     : Summary{0, total, 0, 0});
-      }
-    } else {
-      Summary s = thread_summary(x, g.my_cnt, g.g0, a.fdB, [&](uint32_t v) { return s_len[v]; },
-                                 bad);
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        Summary o = shfl_up_summary(s, d);
-        if (lane >= d) s = combine(o, s);
-      }
-      if (lane == 31) s_warp[warp] = s;
-      __syncthreads();
-      if (tid == 0) {
-        Summary t{0, 0, 0, 0};
-        for (int w = 0; w < kEncThreads / 32; ++w) t = combine(t, s_warp[w]);
-        store_summary(a.tiles[tile], t);
-      }
-    }
-    __syncthreads();
-  }
+  for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
+    summary_tile(a, tile, s_len, s_wsum, s_warp, bad);
   if (bad) set_error(a.st, HZ_ERR_ARG, 0x200);  // a byte without a code (caller's code table)
 }
 
@@ -236,8 +46,6 @@ __global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs 
 // Each CTA scans kScanTilesPerCta consecutive tile summaries (4 per thread);
 // CTAs take their index from a ticket and find their exclusive prefix by a
 // look-back over the aggregates of earlier CTAs (at most 128 of them).
-constexpr int kScanThreads = 1024;
-constexpr int kScanPerThread = kScanTilesPerCta / kScanThreads;
 
 __global__ void __launch_bounds__(kScanThreads) encode_scan_kernel(EncodeArgs a) {
   __shared__ Summary s_warp[kScanThreads / 32];
@@ -360,461 +168,24 @@ __global__ void __launch_bounds__(kScanThreads) encode_scan_kernel(EncodeArgs a)
       a.tiles[t0 + k].pre_O = s.O;
       a.tiles[t0 + k].pre_b = s.b;
       s = apply(s, mine[k]);
-      if (t0 + k == nt - 1) {
-        // the thread holding the last tile knows the whole stream
-        const uint64_t rec_base = kHeaderBytes + ((a.flags & kFlagIndex) ? 4ull * a.nb : 0ull);
-        const uint64_t words = s.O + 1 + ceil32(s.b);
-        const uint64_t size = rec_base + 4 * words;
-        *a.out_len = size;
-        bool ok = st->error == 0 && !s_abort;
-        if (size > a.out_cap || words > 0xFFFFFFFFull) {
-          set_error(st, HZ_ERR_CAPACITY, 0x203);
-          ok = false;
-        }
-        st->enc_ok = ok ? 1u : 0u;
-      }
+      if (t0 + k == nt - 1) finish_stream(a, s, s_abort != 0);  // the last tile's thread
     }
-  }
-}
-
-// =================================================================== pass 3
-struct PackShared {
-  EncodeArgs a;         // the launch arguments, read by the per-tile functions
-  uint32_t entry[256];  // code << 6 | len, valid for codes of up to 26 bits
-  uint32_t len[256];
-  uint32_t code_lo[256];
-  uint32_t code_hi[256];
-  uint32_t wsum[kEncThreads / 32];
-  Summary warp_sum[kEncThreads / 32];
-  uint32_t prev_bits;
-  __align__(16) uint32_t stage[kEncStageWords + 4];
-};
-
-template <bool kLong>
-__device__ __forceinline__ void lookup(const PackShared& sh, uint32_t sym, uint32_t& l,
-                                       uint64_t& c) {
-  if (!kLong) {
-    const uint32_t e = sh.entry[sym];
-    l = e & 63u;
-    c = e >> 6;
-  } else {
-    l = sh.len[sym];
-    c = ((uint64_t)sh.code_hi[sym] << 32) | sh.code_lo[sym];
-  }
-}
-
-// The r (< 32) payload bits just before input position `pos` (all inside the
-// record that continues at `pos`), right-aligned.
-template <bool kLong>
-__device__ uint32_t bits_before(const PackShared& sh, const uint8_t* in, uint32_t pos,
-                                uint32_t r) {
-  uint64_t v = 0;
-  uint32_t got = 0;
-  int64_t j = (int64_t)pos - 1;
-  while (got < r && j >= 0) {
-    uint32_t l;
-    uint64_t c;
-    lookup<kLong>(sh, in[j], l, c);
-    if (got < 64) v |= c << got;
-    got += l;
-    --j;
-  }
-  return (uint32_t)(v & ((1u << r) - 1u));
-}
-
-// Pack one thread's 32 cached entries (code << 6 | len) MSB-first into
-// st[wrel...], starting `nacc` bits into word wrel.  A word that may hold an
-// earlier thread's bits (the first one, when nacc != 0) or a later thread's
-// (the last, partial one) is combined with atomicOr.
-template <bool kPair>
-__device__ __forceinline__ void pack_entries(const uint32_t (&e)[kEncSymPerThread], uint32_t* st,
-                                             uint32_t wrel, uint32_t nacc) {
-  bool first_shared = nacc != 0;
-  uint64_t acc = 0;
-  auto push = [&](uint32_t c, uint32_t l) {
-    acc = (acc << l) | c;
-    nacc += l;
-    if (nacc >= 32) {
-      nacc -= 32;
-      const uint32_t v = (uint32_t)(acc >> nacc);
-      if (first_shared) atomicOr(st + wrel, v);
-      else st[wrel] = v;
-      first_shared = false;
-      ++wrel;
-    }
-  };
-  if (kPair) {
-#pragma unroll
-    for (int j = 0; j < kEncSymPerThread / 2; ++j) {
-      const uint32_t ea = e[2 * j], eb = e[2 * j + 1];
-      const uint32_t lb = eb & 63u;
-      push(((ea >> 6) << lb) | (eb >> 6), (ea & 63u) + lb);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < kEncSymPerThread; ++i) push(e[i] >> 6, e[i] & 63u);
-  }
-  if (nacc) atomicOr(st + wrel, (uint32_t)(acc << (32 - nacc)));
-}
-
-// Write stage[off .. end) to gbase[off .. end) with 16-byte stores where a
-// whole aligned chunk is inside the range, skipping index skip_i.
-__device__ __forceinline__ void copy_out(const uint32_t* stage, uint32_t* gbase, uint32_t off,
-                                         uint32_t end, uint32_t skip_i) {
-  const uint32_t nchunks = (end + 3) >> 2;
-  for (uint32_t c = threadIdx.x; c < nchunks; c += kEncThreads) {
-    const uint32_t i0 = c << 2;
-    if (i0 >= off && i0 + 4 <= end && (skip_i < i0 || skip_i >= i0 + 4)) {
-      *reinterpret_cast<uint4*>(gbase + i0) = *reinterpret_cast<const uint4*>(stage + i0);
-    } else {
-#pragma unroll
-      for (uint32_t k = 0; k < 4; ++k) {
-        const uint32_t i = i0 + k;
-        if (i >= off && i < end && i != skip_i) gbase[i] = stage[i];
-      }
-    }
-  }
-}
-
-// Single-record path: the tile lies inside one record (which may start at its
-// first symbol) and codes have at most 26 bits; thread positions come from a
-// plain scan of bit counts.
-template <bool kPair>
-__device__ __noinline__ void pack_tile_single(PackShared& sh, uint32_t tile, const TileGeom g,
-                                                 uint32_t* rec_words) {
-  const EncodeArgs& a = sh.a;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const ScanState S{a.tiles[tile].pre_O, a.tiles[tile].pre_b};
-  const uint64_t O1 = g.starts_record ? S.O + 1 + ceil32(S.b) : S.O;
-  const uint32_t b0 = g.starts_record ? 0u : S.b;
-
-  uint32_t x[kEncSymPerThread / 4];
-  load_symbols(a.in + g.g0, g.my_cnt, x);
-  uint32_t e[kEncSymPerThread];
-  uint32_t bits = 0;
-#pragma unroll
-  for (int i = 0; i < kEncSymPerThread; ++i) {
-    e[i] = i < g.my_cnt ? sh.entry[sym_of(x, i)] : 0u;
-    bits += e[i] & 63u;
-  }
-  uint32_t inc = bits;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
-    if (lane >= d) inc += o;
-  }
-  if (lane == 31) sh.wsum[warp] = inc;
-  __syncthreads();
-  uint32_t wpre = 0, total = 0;
-#pragma unroll
-  for (int w = 0; w < kEncThreads / 32; ++w) {
-    const uint32_t v = sh.wsum[w];
-    wpre += w < warp ? v : 0u;
-    total += v;
-  }
-  const uint32_t ex = wpre + inc - bits;
-  const uint32_t bend = b0 + total;
-  const uint64_t W0 = O1 + 1 + (b0 >> 5);
-  const uint32_t nwords = ((bend - 1) >> 5) - (b0 >> 5) + 1;
-  const uint32_t off = (uint32_t)((((uintptr_t)rec_words) >> 2) + W0) & 3u;
-  if (total == 0 || off + nwords > (uint32_t)kEncStageWords + 4) {
-    if (tid == 0) set_error(a.st, HZ_ERR_ARG, 0x206);
-    return;  // uniform
-  }
-  const uint32_t r_prev = b0 & 31u;
-  for (uint32_t i = tid; i < off + nwords; i += kEncThreads) sh.stage[i] = 0;
-  if (tid == 0 && r_prev) sh.prev_bits = bits_before<false>(sh, a.in, g.lo, r_prev);
-  __syncthreads();
-  if (tid == 0 && r_prev) sh.stage[off] = sh.prev_bits << (32 - r_prev);
-  __syncthreads();
-  if (bits) {
-    const uint32_t p = b0 + ex;
-    pack_entries<kPair>(e, sh.stage + off, (p >> 5) - (b0 >> 5), p & 31u);
-  }
-  __syncthreads();
-  // the last word belongs to the next tile when the record goes on mid-word
-  const bool skip_last = !g.ends_record && (bend & 31u) != 0;
-  copy_out(sh.stage, rec_words + (W0 - off), off, off + nwords - (skip_last ? 1u : 0u),
-           0xFFFFFFFFu);
-  if (tid == 0) {
-    if (g.ends_record) rec_words[O1] = bend;  // this tile holds the record's last symbol
-    if (g.starts_record && (a.flags & kFlagIndex))
-      reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[fast_div(g.lo, a.fdB)] = (uint32_t)O1;
-  }
-}
-
-// Chunked path: B is a multiple of 32, so records start and end only at the
-// boundaries of the threads' 32-symbol chunks, and codes have at most 26
-// bits.  Each chunk lies inside one record; a thread's start state comes from
-// a CTA scan of chunk summaries.
-template <bool kPair>
-__device__ __noinline__ void pack_tile_chunked(PackShared& sh, uint32_t tile, const TileGeom g,
-                                                  uint32_t* rec_words) {
-  const EncodeArgs& a = sh.a;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const ScanState S_s{a.tiles[tile].pre_O, a.tiles[tile].pre_b};
-
-  uint32_t x[kEncSymPerThread / 4];
-  load_symbols(a.in + g.g0, g.my_cnt, x);
-  uint32_t e[kEncSymPerThread];
-  uint32_t bits = 0;
-#pragma unroll
-  for (int i = 0; i < kEncSymPerThread; ++i) {
-    e[i] = i < g.my_cnt ? sh.entry[sym_of(x, i)] : 0u;
-    bits += e[i] & 63u;
-  }
-  const bool starts = g.my_cnt > 0 && fast_mod(g.g0, a.fdB) == 0;
-  const uint32_t gend = g.g0 + (uint32_t)g.my_cnt;
-  const bool ends = g.my_cnt > 0 && (fast_mod(gend, a.fdB) == 0 || gend == (uint32_t)a.n);
-  const Summary mine = starts ? Summary{1, 0, 0, bits} : Summary{0, bits, 0, 0};
-  Summary inc = mine;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    Summary o = shfl_up_summary(inc, d);
-    if (lane >= d) inc = combine(o, inc);
-  }
-  Summary ex = shfl_up_summary(inc, 1);
-  if (lane == 0) ex = Summary{0, 0, 0, 0};
-  if (lane == 31) sh.warp_sum[warp] = inc;
-  __syncthreads();
-  Summary wpre{0, 0, 0, 0}, agg{0, 0, 0, 0};
-#pragma unroll
-  for (int w = 0; w < kEncThreads / 32; ++w) {
-    const Summary v = sh.warp_sum[w];
-    if (w < warp) wpre = combine(wpre, v);
-    agg = combine(agg, v);
-  }
-  const ScanState S_t = apply(S_s, combine(wpre, ex));  // before my chunk
-  const uint64_t myO = starts ? S_t.O + 1 + ceil32(S_t.b) : S_t.O;
-  const uint32_t myb = starts ? 0u : S_t.b;
-  const ScanState S_e = apply(S_s, agg);
-  const uint64_t w_first = g.starts_record ? S_s.O + 1 + ceil32(S_s.b) : S_s.O + 1 + (S_s.b >> 5);
-  const uint64_t w_last = S_e.O + 1 + ((S_e.b - 1) >> 5);
-  const uint32_t off = (uint32_t)((((uintptr_t)rec_words) >> 2) + w_first) & 3u;
-  if (S_e.b == 0 || w_last < w_first || w_last - w_first + off >= (uint64_t)kEncStageWords + 4) {
-    if (tid == 0) set_error(a.st, HZ_ERR_ARG, 0x207);
-    return;  // uniform
-  }
-  const uint32_t nwords = (uint32_t)(w_last - w_first + 1);
-  const bool skip_last = !g.ends_record && (S_e.b & 31u) != 0;
-  // the delimiter of a record that starts here but ends in a later tile is
-  // written by that later tile
-  const uint32_t skip_i = (!g.ends_record && S_e.O >= w_first)
-                              ? off + (uint32_t)(S_e.O - w_first) : 0xFFFFFFFFu;
-  const uint32_t r_prev = g.starts_record ? 0u : (S_s.b & 31u);
-  for (uint32_t i = tid; i < off + nwords; i += kEncThreads) sh.stage[i] = 0;
-  if (tid == 0 && r_prev) sh.prev_bits = bits_before<false>(sh, a.in, g.lo, r_prev);
-  __syncthreads();
-  if (tid == 0 && r_prev) sh.stage[off] = sh.prev_bits << (32 - r_prev);
-  __syncthreads();
-  uint32_t* st = sh.stage + off;
-  if (g.my_cnt > 0) {
-    if (bits) pack_entries<kPair>(e, st, (uint32_t)(myO + 1 + (myb >> 5) - w_first), myb & 31u);
-    if (ends) {
-      // last chunk of a record: its delimiter is now known
-      if (myO >= w_first) st[myO - w_first] = myb + bits;
-      else rec_words[myO] = myb + bits;
-    }
-    if (starts && (a.flags & kFlagIndex))
-      reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[fast_div(g.g0, a.fdB)] = (uint32_t)myO;
-  }
-  __syncthreads();
-  copy_out(sh.stage, rec_words + (w_first - off), off, off + nwords - (skip_last ? 1u : 0u),
-           skip_i);
-}
-
-// Writer for one thread's words in the general path: words inside the current
-// staging window go to shared memory, others are dropped (another window pass
-// writes them).
-struct Emitter {
-  uint32_t* stage;
-  uint64_t win_lo, win_hi;
-  __device__ __forceinline__ void put(uint64_t w, uint32_t v, bool shared_word) {
-    if (w >= win_lo && w < win_hi) {
-      uint32_t* p = stage + (w - win_lo);
-      if (shared_word) atomicOr(p, v);
-      else *p = v;
-    }
-  }
-};
-
-// General path: record starts anywhere in the tile, codes of any length.
-template <bool kLong>
-__device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, const TileGeom g,
-                                                  uint32_t* rec_words) {
-  const EncodeArgs& a = sh.a;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t n = (uint32_t)a.n;
-  const uint32_t B = a.fdB.d;
-  uint32_t x[kEncSymPerThread / 4];
-  load_symbols(a.in + g.g0, g.my_cnt, x);
-  bool bad = false;
-  const Summary s = thread_summary(
-      x, g.my_cnt, g.g0, a.fdB,
-      [&](uint32_t v) {
-        uint32_t l;
-        uint64_t c;
-        lookup<kLong>(sh, v, l, c);
-        return l;
-      },
-      bad);
-  Summary inc = s;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    Summary o = shfl_up_summary(inc, d);
-    if (lane >= d) inc = combine(o, inc);
-  }
-  Summary ex = shfl_up_summary(inc, 1);
-  if (lane == 0) ex = Summary{0, 0, 0, 0};
-  if (lane == 31) sh.warp_sum[warp] = inc;
-  __syncthreads();
-  Summary wpre{0, 0, 0, 0}, agg{0, 0, 0, 0};
-  for (int w = 0; w < kEncThreads / 32; ++w) {
-    if (w < warp) wpre = combine(wpre, sh.warp_sum[w]);
-    agg = combine(agg, sh.warp_sum[w]);
-  }
-  ex = combine(wpre, ex);
-
-  const ScanState S_s{a.tiles[tile].pre_O, a.tiles[tile].pre_b};
-  const ScanState S_e = apply(S_s, agg);
-  const uint64_t w_first = g.starts_record ? S_s.O + 1 + ceil32(S_s.b) : S_s.O + 1 + (S_s.b >> 5);
-  const uint64_t w_last = S_e.O + 1 + ((S_e.b - 1) >> 5);
-  const bool skip_last = !g.ends_record && (S_e.b & 31u) != 0;
-  const bool skip_open = !g.ends_record && S_e.O >= w_first && S_e.O <= w_last;
-  const uint32_t r_prev = g.starts_record ? 0u : (S_s.b & 31u);
-  if (S_e.b == 0 || w_last < w_first || w_last - w_first > 3ull * kEncTile + 64) {
-    if (tid == 0) set_error(a.st, HZ_ERR_ARG, 0x204);
-    return;  // uniform
-  }
-  if (tid == 0) sh.prev_bits = r_prev ? bits_before<kLong>(sh, a.in, g.lo, r_prev) : 0u;
-  const ScanState S_t = apply(S_s, ex);  // state before my first symbol
-  const uint32_t r0 = fast_mod(g.g0, a.fdB);
-  const uint32_t first_start = r0 == 0 ? 0u : B - r0;
-  // one past the last symbol of my first record
-  const uint32_t first_end = (uint32_t)min((uint64_t)g.g0 - r0 + B, (uint64_t)n);
-
-  for (uint64_t wlo = w_first; wlo <= w_last; wlo += kEncStageWords) {
-    const uint64_t whi = wlo + kEncStageWords < w_last + 1 ? wlo + kEncStageWords : w_last + 1;
-    for (int i = tid; i < kEncStageWords; i += kEncThreads) sh.stage[i] = 0;
-    __syncthreads();
-    if (tid == 0 && wlo == w_first && r_prev) sh.stage[0] = sh.prev_bits << (32 - r_prev);
-    __syncthreads();
-    Emitter em{sh.stage, wlo, whi};
-    ScanState cur = S_t;
-    uint64_t wcur = cur.O + 1 + (cur.b >> 5);
-    uint32_t nacc = cur.b & 31u;
-    bool first_shared = nacc != 0;
-    uint64_t acc = 0;
-    uint32_t next_start = first_start;
-    uint32_t next_end = first_end;
-#pragma unroll
-    for (int i = 0; i < kEncSymPerThread; ++i) {
-      if (i < g.my_cnt) {
-        if ((uint32_t)i == next_start) {
-          if (nacc) em.put(wcur, (uint32_t)(acc << (32 - nacc)), true);
-          cur.O = cur.O + 1 + ceil32(cur.b);
-          cur.b = 0;
-          if ((a.flags & kFlagIndex) && wlo == w_first)
-            reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[fast_div(g.g0 + i, a.fdB)] =
-                (uint32_t)cur.O;
-          wcur = cur.O + 1;
-          nacc = 0;
-          acc = 0;
-          first_shared = false;
-          next_start += B;
-        }
-        uint32_t l;
-        uint64_t c;
-        lookup<kLong>(sh, sym_of(x, i), l, c);
-        if (kLong && l > 32) {
-          const uint32_t lh = l - 32;
-          acc = (acc << lh) | (c >> 32);
-          nacc += lh;
-          if (nacc >= 32) {
-            nacc -= 32;
-            em.put(wcur++, (uint32_t)(acc >> nacc), first_shared);
-            first_shared = false;
-          }
-          acc = (acc << 32) | (c & 0xFFFFFFFFull);
-          em.put(wcur++, (uint32_t)(acc >> nacc), first_shared);
-          first_shared = false;
-        } else {
-          acc = (acc << l) | c;
-          nacc += l;
-          if (nacc >= 32) {
-            nacc -= 32;
-            em.put(wcur++, (uint32_t)(acc >> nacc), first_shared);
-            first_shared = false;
-          }
-        }
-        cur.b += l;
-        if (g.g0 + (uint32_t)i + 1 == next_end) {
-          // last symbol of a record: its delimiter is now known
-          if (cur.O >= wlo && cur.O < whi) sh.stage[cur.O - wlo] = cur.b;
-          else if (cur.O < w_first && wlo == w_first) rec_words[cur.O] = cur.b;
-          next_end = (uint32_t)min((uint64_t)next_end + B, (uint64_t)n);
-        }
-      }
-    }
-    if (nacc && g.my_cnt) em.put(wcur, (uint32_t)(acc << (32 - nacc)), true);
-    __syncthreads();
-    const uint64_t cnt_w = whi - wlo;
-    for (uint64_t i = tid; i < cnt_w; i += kEncThreads) {
-      const uint64_t w = wlo + i;
-      if ((skip_last && w == w_last) || (skip_open && w == S_e.O)) continue;
-      rec_words[w] = sh.stage[i];
-    }
-    __syncthreads();
-  }
-}
-
-// Tile loops, one per path, each compiled on its own so that the common
-// paths keep their registers.
-template <int kMode>  // 0: single-record/chunked with pairs, 1: same with single codes
-__device__ __forceinline__ void pack_tiles_fast(const EncodeArgs& a, PackShared& sh,
-                                             uint32_t* rec_words) {
-  const bool chunked_ok = a.fdB.d % kEncSymPerThread == 0;
-  for (uint32_t i = blockIdx.x; i < a.ntiles; i += gridDim.x) {
-    const uint32_t tile = a.ntiles - 1 - i;  // last tiles first: their input is still in L2
-    const TileGeom g = tile_geom(tile, (uint32_t)a.n, a.fdB);
-    if (!g.interior_start) pack_tile_single<kMode == 0>(sh, tile, g, rec_words);
-    else if (chunked_ok) pack_tile_chunked<kMode == 0>(sh, tile, g, rec_words);
-    else pack_tile_general<false>(sh, tile, g, rec_words);
-    __syncthreads();
-  }
-}
-
-__device__ __forceinline__ void pack_tiles_long(const EncodeArgs& a, PackShared& sh,
-                                             uint32_t* rec_words) {
-  for (uint32_t i = blockIdx.x; i < a.ntiles; i += gridDim.x) {
-    const uint32_t tile = a.ntiles - 1 - i;
-    pack_tile_general<true>(sh, tile, tile_geom(tile, (uint32_t)a.n, a.fdB), rec_words);
-    __syncthreads();
   }
 }
 
 __global__ void __launch_bounds__(kEncThreads, 3) encode_pack_kernel(EncodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   PackShared& sh = *reinterpret_cast<PackShared*>(smem_raw);
-  const CodeTable* ct = &a.st->codes;
   // size, capacity, time-out or code errors were found before packing
   if (!a.st->enc_ok || a.st->error) return;
-  const uint32_t maxlen = ct->maxlen;
-  for (int s = threadIdx.x; s < 256; s += kEncThreads) {
-    const uint32_t l = ct->len[s];
-    const uint64_t c = ct->code[s];
-    sh.len[s] = l;
-    sh.code_lo[s] = (uint32_t)c;
-    sh.code_hi[s] = (uint32_t)(c >> 32);
-    sh.entry[s] = (uint32_t)(c << 6) | l;
-  }
-  if (threadIdx.x == 0) sh.a = a;
+  const uint32_t maxlen = a.st->codes.maxlen;
+  pack_load_tables(sh, a);
   __syncthreads();
-  uint32_t* rec_words = reinterpret_cast<uint32_t*>(
-      a.out + kHeaderBytes + ((a.flags & kFlagIndex) ? 4ull * a.nb : 0ull));
-  if (maxlen <= 16) pack_tiles_fast<0>(a, sh, rec_words);
-  else if (maxlen <= 26) pack_tiles_fast<1>(a, sh, rec_words);
-  else pack_tiles_long(a, sh, rec_words);
+  for (uint32_t i = blockIdx.x; i < a.ntiles; i += gridDim.x) {
+    // last tiles first: their input is still in L2 from the length-summing pass
+    pack_one_tile(sh, a.ntiles - 1 - i, maxlen);
+    __syncthreads();
+  }
 }
 
 cudaError_t launch_encode_summary(const EncodeArgs& a, int num_sms, cudaStream_t s) {

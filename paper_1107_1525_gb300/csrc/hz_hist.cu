@@ -8,26 +8,9 @@
 // 16-symbol alphabet) causes no intra-warp serialisation.  Warps of one CTA
 // share the copies through shared-memory atomics.  At the end every CTA folds
 // its copies and adds its 256 sums to the global counters.
-#include "hz_internal.cuh"
+#include "hz_hist_dev.cuh"
 
 namespace hz {
-
-constexpr int kHistThreads = 512;
-constexpr int kHistCtasPerSm = 4;
-
-__device__ __forceinline__ void count_word(uint32_t* col, uint32_t w) {
-  atomicAdd(col + ((w & 0xFFu) << 5), 1u);
-  atomicAdd(col + (((w >> 8) & 0xFFu) << 5), 1u);
-  atomicAdd(col + (((w >> 16) & 0xFFu) << 5), 1u);
-  atomicAdd(col + ((w >> 24) << 5), 1u);
-}
-
-__device__ __forceinline__ void count_vec(uint32_t* col, uint4 v) {
-  count_word(col, v.x);
-  count_word(col, v.y);
-  count_word(col, v.z);
-  count_word(col, v.w);
-}
 
 __global__ void __launch_bounds__(kHistThreads) histogram_kernel(const uint8_t* __restrict__ in,
                                                                  uint64_t n, DevState* st) {

@@ -1,0 +1,157 @@
+// hz_tune.cu -- the autotuner behind hz_autotune (declared in include/hz.h)
+// and its JSON cache.
+//
+// Per input-size class it times compress + decompress round trips of a slice
+// of the caller's sample for every candidate block size, keeps the fastest
+// one whose per-block format overhead stays within 1 % (Sec. 2.1: each block
+// costs 32-63 bits), and then times the decoder's table width on the largest
+// class.  The result lives in the context; HZ_TUNE_CACHE names a file that
+// stores it across processes.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "hz_internal.cuh"
+
+uint32_t hz_ctx_block_size(hz_ctx* c, uint64_t n);
+void hz_ctx_set_tuned(hz_ctx* c, const uint32_t* B, int lut_bits);
+void hz_ctx_get_tuned(hz_ctx* c, uint32_t* B, int* lut_bits);
+int hz_ctx_device(hz_ctx* c);
+
+namespace {
+
+constexpr uint64_t kClassSize[4] = {64ull << 10, 1ull << 20, 16ull << 20, 256ull << 20};
+constexpr uint32_t kCandB[5] = {4096, 8192, 16384, 32768, 65536};
+constexpr int kCandW[3] = {10, 11, 12};
+
+void write_cache(const uint32_t* B, int W) {
+  const char* path = getenv("HZ_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "w");
+  if (!f) return;
+  fprintf(f, "{\"version\": 1, \"block_size\": [%u, %u, %u, %u], \"lut_bits\": %d}\n", B[0], B[1],
+          B[2], B[3], W);
+  fclose(f);
+}
+
+}  // namespace
+
+void hz_tune_load_cache(hz_ctx* c) {
+  const char* path = getenv("HZ_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char buf[512] = {0};
+  const size_t got = fread(buf, 1, sizeof(buf) - 1, f);
+  fclose(f);
+  buf[got] = 0;
+  uint32_t B[4];
+  int W = 0;
+  const char* p = strstr(buf, "\"block_size\"");
+  const char* q = strstr(buf, "\"lut_bits\"");
+  if (!p || !q) return;
+  if (sscanf(p, "\"block_size\": [%u, %u, %u, %u]", &B[0], &B[1], &B[2], &B[3]) != 4) return;
+  if (sscanf(q, "\"lut_bits\": %d", &W) != 1) return;
+  for (int k = 0; k < 4; ++k)
+    if (B[k] == 0 || B[k] > hz::kMaxBlock) return;
+  if (W < hz::kLutMinBits || W > hz::kLutMaxBits) return;
+  hz_ctx_set_tuned(c, B, W);
+}
+
+extern "C" hz_status hz_autotune(hz_ctx* c, const uint8_t* d_sample, uint64_t n, void* stream) {
+  if (!c || !d_sample || n < 4096 || n > 0xFFFFFFFFull) return HZ_ERR_ARG;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(hz_ctx_device(c));
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t m_max = n < kClassSize[3] ? n : kClassSize[3];
+  const uint64_t cap = hz_compress_bound(m_max, 4096);
+  uint8_t *d_out = nullptr, *d_dec = nullptr;
+  uint64_t* d_len = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  hz_status result = HZ_OK;
+  uint32_t best_B[4];
+  int best_W = 12;
+  uint32_t old_B[4];
+  int old_W = 12;
+  hz_ctx_get_tuned(c, old_B, &old_W);
+  if (cudaMalloc(&d_out, cap) != cudaSuccess || cudaMalloc(&d_dec, m_max) != cudaSuccess ||
+      cudaMalloc(&d_len, 2 * sizeof(uint64_t)) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    result = HZ_ERR_NOMEM;
+  }
+  auto round_trip = [&](uint64_t m, uint32_t B, int iters, float* ms, uint64_t* len) -> hz_status {
+    hz_status st = HZ_OK;
+    cudaEventRecord(e0, s);
+    for (int it = 0; it < iters && st == HZ_OK; ++it) {
+      st = hz_compress(c, d_sample, m, B, nullptr, d_out, cap, d_len, s);
+      uint64_t slen = 0;
+      if (st == HZ_OK && it == 0) {
+        // the first stream's size, for the decode and the overhead check
+        cudaMemcpyAsync(&slen, d_len, 8, cudaMemcpyDeviceToHost, s);
+        st = hz_sync(c, s);
+        *len = slen;
+      }
+      if (st == HZ_OK) st = hz_decompress(c, d_out, *len, d_dec, m, d_len + 1, s);
+    }
+    cudaEventRecord(e1, s);
+    if (st == HZ_OK) st = hz_sync(c, s);
+    if (st == HZ_OK) cudaEventElapsedTime(ms, e0, e1);
+    return st;
+  };
+  for (int k = 0; k < 4 && result == HZ_OK; ++k) {
+    const uint64_t m = n < kClassSize[k] ? n : kClassSize[k];
+    const int iters = (int)((256ull << 20) / m) < 1 ? 1 : ((256ull << 20) / m > 64 ? 64 : (int)((256ull << 20) / m));
+    float best = 1e30f;
+    best_B[k] = hz_ctx_block_size(c, m);
+    for (uint32_t B : kCandB) {
+      float ms = 0;
+      uint64_t len = 0;
+      // warm-up, then the timed round trips
+      if (round_trip(m, B, 1, &ms, &len) != HZ_OK) continue;
+      const uint64_t nb = (m + B - 1) / B;
+      if (nb * 8 > len / 100) continue;  // up to 63 bits + delimiter per block: keep within 1 %
+      if (round_trip(m, B, iters, &ms, &len) != HZ_OK) continue;
+      if (ms < best) {
+        best = ms;
+        best_B[k] = B;
+      }
+    }
+  }
+  if (result == HZ_OK) {
+    // decoder table width, on the largest class with its chosen block size
+    const uint64_t m = m_max;
+    float best = 1e30f;
+    uint64_t len = 0;
+    hz_compress(c, d_sample, m, best_B[3], nullptr, d_out, cap, d_len, s);
+    cudaMemcpyAsync(&len, d_len, 8, cudaMemcpyDeviceToHost, s);
+    if (hz_sync(c, s) == HZ_OK) {
+      for (int W : kCandW) {
+        hz_set_option(c, HZ_OPT_DECODE_LUT_BITS, W);
+        float ms = 0;
+        hz_decompress(c, d_out, len, d_dec, m, d_len + 1, s);  // warm-up
+        cudaEventRecord(e0, s);
+        for (int it = 0; it < 8; ++it) hz_decompress(c, d_out, len, d_dec, m, d_len + 1, s);
+        cudaEventRecord(e1, s);
+        if (hz_sync(c, s) != HZ_OK) continue;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_W = W;
+        }
+      }
+    }
+    hz_ctx_set_tuned(c, best_B, best_W);
+    write_cache(best_B, best_W);
+  } else {
+    hz_ctx_set_tuned(c, old_B, old_W);
+  }
+  cudaFree(d_out);
+  cudaFree(d_dec);
+  cudaFree(d_len);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (prev >= 0) cudaSetDevice(prev);
+  return result;
+}

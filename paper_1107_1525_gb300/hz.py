@@ -23,14 +23,15 @@ STATUS_NAMES = {0: "HZ_OK", 1: "HZ_PENDING", -1: "HZ_ERR_ARG", -2: "HZ_ERR_CAPAC
                 -6: "HZ_ERR_TIMEOUT", -7: "HZ_ERR_CUDA"}
 HEADER_BYTES = 280
 HZ_OPT_INDEX, HZ_OPT_PROFILE, HZ_OPT_DECODE_LUT_BITS = 1, 2, 3
-HZ_OPT_DECODE_THREADS, HZ_OPT_AUTOTUNE = 4, 5
+HZ_OPT_DECODE_THREADS, HZ_OPT_AUTOTUNE, HZ_OPT_BATCH_PLAIN = 4, 5, 6
 HZ_OP_COMPRESS, HZ_OP_DECOMPRESS = 0, 1
 
 # the C symbols include/hz.h declares (checked by the test suite)
 EXPORTS = ("hz_create", "hz_destroy", "hz_compress_bound", "hz_build_codes", "hz_compress",
            "hz_decompress", "hz_sync", "hz_compress_host", "hz_decompress_host",
            "hz_set_option", "hz_get_option", "hz_launch_count", "hz_profile_read",
-           "hz_kernel_name", "hz_submit", "hz_poll", "hz_compress_noalloc")
+           "hz_kernel_name", "hz_submit", "hz_poll", "hz_compress_noalloc", "hz_autotune",
+           "hz_tuned_block_size")
 
 
 class HzError(RuntimeError):
@@ -80,6 +81,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hz_submit": (i32, [vp, ctypes.POINTER(HzRequest), u32, ctypes.POINTER(u64)]),
         "hz_poll": (i32, [vp, u64, i64, vp, vp]),
         "hz_compress_noalloc": (i32, [vp, u64, u32, vp, u64, vp, vp, vp]),
+        "hz_autotune": (i32, [vp, vp, u64, vp]),
+        "hz_tuned_block_size": (u32, [vp, u64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -204,6 +207,15 @@ def hz_compress_noalloc(d_in, n: int, block_size: int, d_out, out_cap: int, d_ou
     return _check(load_library().hz_compress_noalloc(_ptr(d_in), n, block_size, _ptr(d_out),
                                                      out_cap, _ptr(d_out_len), _ptr(d_status),
                                                      _stream(stream)), "hz_compress_noalloc")
+
+
+def hz_autotune(ctx: Context, d_sample, n: int, stream=None) -> int:
+    return _check(ctx._lib.hz_autotune(ctx.handle, _ptr(d_sample), n, _stream(stream)),
+                  "hz_autotune")
+
+
+def hz_tuned_block_size(ctx: Context, n: int) -> int:
+    return int(ctx._lib.hz_tuned_block_size(ctx.handle, n))
 
 
 def hz_sync(ctx: Context, stream=None) -> int:
