@@ -7,6 +7,11 @@ workload is the 1 GiB buffer of 64 MiB segments cycling Zipf(1.1),
 geometric(0.3), uniform-256 and uniform-16 bytes, in 64 KiB blocks.  Inputs
 (1 GiB) are larger than the 129 MB L2, so no flush is needed between steps.
 
+On one GPU the line also carries the batched workload (4096 buffers of uneven
+sizes through hz_submit, against plain one-launch-sequence-per-buffer mode)
+under "batched", and the open-loop request replay (Poisson 20k req/s of mixed
+compress / decompress requests) under "serving".
+
 Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead,
 on a bounded sample of the same workload.
 """
@@ -218,6 +223,210 @@ def run_reference(args, world, rank, pg):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched workload
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def run_batched(args, hz, dev):
+    """4096 independent buffers, lengths log-uniform in [4 KiB, 16 MiB], buffer i
+    Zipf(s_i) with s_i ~ U[0.6, 1.6]; block size from the tuned table.  The whole
+    set goes to hz_submit as one submission (one CUDA graph of persistent kernels)
+    and, for the baseline, through plain mode (hz_compress / hz_decompress per
+    buffer, one stream).  Times are host wall clock from hz_submit to hz_poll."""
+    import torch
+
+    import datagen
+    lens, s = datagen.batch_sizes(count=args.batch_count, seed=3)
+    offs = np.zeros(len(lens) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum((lens + 255) // 256 * 256)
+    arena = torch.empty(int(offs[-1]), dtype=torch.uint8, device=dev)
+    for i in range(len(lens)):
+        arena[offs[i]:offs[i] + lens[i]] = datagen.sample_iid(
+            datagen.zipf_pmf(float(s[i])), int(lens[i]), (3 << 20) + i, dev)
+    ctx = hz.Context(dev.index or 0)
+    lib = hz.load_library()
+    Bs = np.array([lib.hz_tuned_block_size(ctx.handle, int(n)) for n in lens])
+    caps = np.array([hz.hz_compress_bound(int(n), int(b)) for n, b in zip(lens, Bs)])
+    coffs = np.zeros(len(lens) + 1, dtype=np.int64)
+    coffs[1:] = np.cumsum((caps + 255) // 256 * 256)
+    out = torch.empty(int(coffs[-1]), dtype=torch.uint8, device=dev)
+    back = torch.empty_like(arena)
+    base_in, base_out, base_back = arena.data_ptr(), out.data_ptr(), back.data_ptr()
+    creqs = [(hz.HZ_OP_COMPRESS, 0, base_in + int(offs[i]), int(lens[i]),
+              base_out + int(coffs[i]), int(caps[i])) for i in range(len(lens))]
+    total = float(lens.sum())
+
+    def run(reqs):
+        t0 = time.perf_counter()
+        t = hz.hz_submit(ctx, reqs)
+        st, per, ol = hz.hz_poll(ctx, t, len(reqs), -1)
+        dt = time.perf_counter() - t0
+        if st or (per != 0).any():
+            raise RuntimeError(f"batch failed: {st} {np.unique(per)}")
+        return dt, ol
+
+    res = {}
+    for mode in ("batched", "plain"):
+        ctx.set_option(hz.HZ_OPT_BATCH_PLAIN, 1 if mode == "plain" else 0)
+        reps = args.batch_reps if mode == "batched" else max(1, args.batch_reps // 3)
+        _, slen = run(creqs)  # warm-up (slot buffers, graph capture)
+        tc = [run(creqs)[0] for _ in range(reps)]
+        dreqs = [(hz.HZ_OP_DECOMPRESS, 0, base_out + int(coffs[i]), int(slen[i]),
+                  base_back + int(offs[i]), int(lens[i])) for i in range(len(lens))]
+        back.zero_()
+        run(dreqs)
+        if not torch.equal(back, arena):
+            raise RuntimeError(f"{mode} batch round trip failed")
+        td = [run(dreqs)[0] for _ in range(reps)]
+        res[mode] = {"compress_gbs": total / statistics.median(tc) / 1e9,
+                     "decompress_gbs": total / statistics.median(td) / 1e9,
+                     "compress_ms_p50": _pct(tc, 50) * 1e3, "compress_ms_p99": _pct(tc, 99) * 1e3,
+                     "decompress_ms_p50": _pct(td, 50) * 1e3,
+                     "decompress_ms_p99": _pct(td, 99) * 1e3, "reps": reps}
+    ctx.close()
+    b, p = res["batched"], res["plain"]
+    return {
+        "workload": f"{len(lens)} buffers, lengths log-uniform [4 KiB, 16 MiB] (seed 3), "
+                    "Zipf(s_i), s_i ~ U[0.6, 1.6], tuned block size",
+        "buffers": int(len(lens)), "total_bytes": int(total),
+        "stream_bytes": int(slen.sum()),
+        "block_sizes": {str(int(k)): int(v) for k, v in zip(*np.unique(Bs, return_counts=True))},
+        "batched": b, "plain": p,
+        "speedup_compress": b["compress_gbs"] / p["compress_gbs"],
+        "speedup_decompress": b["decompress_gbs"] / p["decompress_gbs"],
+        "timing": "host wall clock, hz_submit to hz_poll, median over reps; latency of the "
+                  "whole batch (every request in it completes with it)",
+    }
+
+
+# ------------------------------------------------------------------ serving workload
+def serve_trace(hz, dev, duration, rate=20000.0, n_arenas=64, arena_bytes=64 * MiB,
+                pool_size=256, seed=5):
+    """Open-loop trace: Poisson arrivals, 60 % compress / 40 % decompress, sizes
+    log-uniform [1 KiB, 64 MiB], data Zipf(s), s ~ U[0.6, 1.6] quantised to
+    n_arenas device-resident arenas of Zipf(0.6 + j / (n_arenas - 1)) bytes.  A
+    compress request takes a slice of arena j; a decompress request takes a
+    stream from a pool of slices compressed beforehand."""
+    import torch
+
+    import datagen
+    arenas = torch.empty(n_arenas * arena_bytes, dtype=torch.uint8, device=dev)
+    for j in range(n_arenas):
+        arenas[j * arena_bytes:(j + 1) * arena_bytes] = datagen.sample_iid(
+            datagen.zipf_pmf(0.6 + j / (n_arenas - 1)), arena_bytes, (seed << 20) + j, dev)
+    rng = np.random.default_rng(seed + 1)
+    ctx = hz.Context(dev.index or 0)
+    pool, pool_src = [], []
+    psize = np.floor(np.exp(rng.uniform(np.log(1024), np.log(arena_bytes), pool_size)))
+    for k in range(pool_size):
+        n = int(psize[k])
+        j = int(rng.integers(n_arenas))
+        off = int(rng.integers(0, arena_bytes - n + 1))
+        x = arenas[j * arena_bytes + off:j * arena_bytes + off + n]
+        pool.append(hz.compress(x, 0, ctx=ctx).clone())
+        pool_src.append(x)
+    ctx.close()
+    t, is_c, size, s = datagen.arrivals(rate=rate, duration=duration, lo=1024,
+                                        hi=arena_bytes, seed=seed)
+    m = t.size
+    items = np.zeros(m, dtype=hz.SERVE_ITEM)
+    items["arrival_s"] = t
+    j = np.clip(np.rint((s - 0.6) * (n_arenas - 1)), 0, n_arenas - 1).astype(np.int64)
+    off = (rng.uniform(size=m) * (arena_bytes - size + 1)).astype(np.int64)
+    src_c = arenas.data_ptr() + j * arena_bytes + off
+    pk = rng.integers(pool_size, size=m)
+    pool_ptr = np.array([p.data_ptr() for p in pool], dtype=np.uint64)
+    pool_len = np.array([p.numel() for p in pool], dtype=np.uint64)
+    pool_n = np.array([x.numel() for x in pool_src], dtype=np.uint64)
+    bound = (280 + 16 * ((size + 4095) // 4096) + 4 * ((size + 3) // 4)).astype(np.uint64)
+    items["op"] = np.where(is_c, 0, 1)
+    items["d_src"] = np.where(is_c, src_c.astype(np.uint64), pool_ptr[pk])
+    items["src_len"] = np.where(is_c, size.astype(np.uint64), pool_len[pk])
+    items["dst_cap"] = np.where(is_c, bound, pool_n[pk])
+    raw = np.where(is_c, size.astype(np.uint64), pool_n[pk]).astype(np.float64)
+    return dict(arenas=arenas, pool=pool, pool_src=pool_src, items=items, raw=raw,
+                is_c=is_c, pk=pk)
+
+
+def serve_stats(items, rec, raw, wall):
+    lat = (rec["done_s"] - items["arrival_s"]) * 1e3
+    ok = rec["status"] == 0
+    comp = items["op"] == 0
+    launches = np.unique(rec["launch"]).size
+    return {"requests": int(items.size), "failed": int((~ok).sum()),
+            "served_gbs": float(raw[ok].sum() / wall / 1e9), "wall_s": wall,
+            "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "max_ms": float(lat.max()),
+            "compress_p50_ms": _pct(lat[comp], 50), "compress_p99_ms": _pct(lat[comp], 99),
+            "decompress_p50_ms": _pct(lat[~comp], 50),
+            "decompress_p99_ms": _pct(lat[~comp], 99),
+            "device_batches": launches, "requests_per_batch": items.size / max(1, launches)}
+
+
+def run_serving(args, hz, dev):
+    import torch
+    tr = serve_trace(hz, dev, args.serve_seconds)
+    items, raw = tr["items"], tr["raw"]
+    ring = torch.empty(args.serve_ring_gib << 30, dtype=torch.uint8, device=dev)
+    ctx = hz.Context(dev.index or 0, mem_budget=40 * 10**9)
+    # warm-up: a burst of the first requests sizes the batch slots and captures the graphs
+    warm = items[: min(items.size, 3000)].copy()
+    warm["arrival_s"] = 0.0
+    hz.hz_serve_replay(ctx, warm, ring)
+    # a sample of requests writes to buffers of their own, so that their bytes
+    # from the mix can be compared with the same requests run alone afterwards
+    k = min(64, items.size)
+    pick = np.sort(np.random.default_rng(11).choice(items.size, k, replace=False))
+    dsts = [torch.empty(int(c), dtype=torch.uint8, device=dev) for c in items["dst_cap"][pick]]
+    items["d_dst"][pick] = [d.data_ptr() for d in dsts]
+    rec, wall = hz.hz_serve_replay(ctx, items, ring)
+    out = serve_stats(items, rec, raw, wall)
+    out["offered_gbs"] = float(raw.sum() / items["arrival_s"][-1] / 1e9)
+    same = 0
+    for q, i in enumerate(pick):
+        n = int(rec[i]["out_len"])
+        if tr["is_c"][i]:
+            alone = hz.compress(_slice(tr, items[i]), 0, ctx=ctx)
+        else:
+            alone = tr["pool_src"][int(tr["pk"][i])]
+        same += int(rec[i]["status"] == 0 and n == alone.numel()
+                    and torch.equal(dsts[q][:n], alone))
+    out["verified_alone_vs_mix"] = f"{same}/{k}"
+    items["d_dst"][pick] = 0
+    # capacity: the first requests all at once, batched and plain
+    cap_n = min(items.size, args.serve_capacity_requests)
+    burst = items[:cap_n].copy()
+    burst["arrival_s"] = 0.0
+    r, w = hz.hz_serve_replay(ctx, burst, ring)
+    out["capacity_gbs"] = float(raw[:cap_n].sum() / w / 1e9)
+    ctx.set_option(hz.HZ_OPT_BATCH_PLAIN, 1)
+    hz.hz_serve_replay(ctx, burst[:200].copy(), ring)
+    r, w = hz.hz_serve_replay(ctx, burst, ring)
+    out["plain_capacity_gbs"] = float(raw[:cap_n].sum() / w / 1e9)
+    out["capacity_speedup"] = out["capacity_gbs"] / out["plain_capacity_gbs"]
+    # plain mode at the same arrival rate, on a prefix of the trace
+    pre = items[items["arrival_s"] < args.serve_plain_seconds].copy()
+    r, w = hz.hz_serve_replay(ctx, pre, ring)
+    ps = serve_stats(pre, r, raw[: pre.size], w)
+    out["plain_at_rate"] = {k2: ps[k2] for k2 in ("requests", "served_gbs", "p50_ms", "p99_ms",
+                                                 "max_ms", "wall_s")}
+    out["plain_at_rate"]["trace_seconds"] = args.serve_plain_seconds
+    ctx.close()
+    out["workload"] = (f"Poisson 20k req/s for {args.serve_seconds} s, 60 % compress / 40 % "
+                       "decompress, sizes log-uniform [1 KiB, 64 MiB], Zipf(s), s ~ U[0.6, 1.6] "
+                       "over 64 device-resident 64 MiB arenas, decompress streams from a pool "
+                       "of 256 pre-compressed slices; 40 GB admission budget")
+    out["latency"] = "completion seen on the host minus scheduled arrival"
+    return out
+
+
+def _slice(tr, item):
+    """The device tensor a compress item reads."""
+    base = tr["arenas"].data_ptr()
+    off = int(item["d_src"]) - base
+    return tr["arenas"][off:off + int(item["src_len"])]
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, world, rank, local, pg):
     import torch
@@ -325,6 +534,17 @@ def run_gpu(args, world, rank, local, pg):
 
     total_bytes = sum_over_ranks(pg, float(n), dev)
     value = total_bytes / (ms_step * 1e-3) / 1e9
+    # the batched and serving workloads run on one GPU only (rank-local replicas
+    # would only repeat them)
+    batched = serving = None
+    if world == 1 and not args.no_batched:
+        with ClockSampler(local) as bclk:
+            batched = run_batched(args, hz, dev)
+        batched["clocks"] = bclk.summary()
+    if world == 1 and not args.no_serving:
+        with ClockSampler(local) as sclk:
+            serving = run_serving(args, hz, dev)
+        serving["clocks"] = sclk.summary()
     if rank != 0:
         return
     # CPU oracle baseline, rank 0 only, bounded sample
@@ -357,6 +577,8 @@ def run_gpu(args, world, rank, local, pg):
                 "ms_per_step": t_e2e * 1e3},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
+        "batched": batched,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
 
@@ -374,6 +596,14 @@ def main():
     ap.add_argument("--cpu-sample-mib", type=int, default=192,
                     help="host sample for the cpu_baseline key of the GPU arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 4096-buffer batch")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-reps", type=int, default=6)
+    ap.add_argument("--no-serving", action="store_true", help="skip the request replay")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-ring-gib", type=int, default=8)
+    ap.add_argument("--serve-capacity-requests", type=int, default=4000)
+    ap.add_argument("--serve-plain-seconds", type=float, default=2.0)
     args = ap.parse_args()
     world, rank, local, pg = dist_setup(args)
     try:

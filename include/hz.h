@@ -186,11 +186,14 @@ hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32_t block_si
 /* ------------------------------------------------------------- options */
 #define HZ_OPT_INDEX 1        /* 1 (default): write the block-offset index */
 #define HZ_OPT_PROFILE 2      /* 1: time every kernel launch with CUDA events */
-#define HZ_OPT_DECODE_LUT_BITS 3  /* decode table width W, 8..12 (default 11) */
+#define HZ_OPT_DECODE_LUT_BITS 3  /* decode table width W, 8..12 (default 12) */
 #define HZ_OPT_DECODE_THREADS 4   /* threads per decode CTA: 128, 256 or 512 */
 #define HZ_OPT_AUTOTUNE 5     /* 1 (default): block_size 0 picks the tuned size */
 #define HZ_OPT_BATCH_PLAIN 6  /* 1: hz_submit runs each request through hz_compress /
                                  hz_decompress in turn (the one-launch-per-buffer baseline) */
+#define HZ_OPT_BATCH_MAX_REQS 7  /* most requests in one device batch when queued
+                                    submissions merge (default 4096; a larger
+                                    single submission still goes alone) */
 
 /* Set an option; HZ_ERR_ARG for an unknown key or value. */
 hz_status hz_set_option(hz_ctx* ctx, int key, int64_t value);
@@ -246,11 +249,17 @@ typedef struct {
 #define HZ_OP_DECOMPRESS 1
 
 /*
- * Queue `count` requests as one batch and return at once with a ticket.
- * Batches are admitted in order against the context's device-memory budget
- * and run on the context's own stream, every request of a batch inside one
- * persistent kernel per phase.  HZ_ERR_BUSY if the batch alone exceeds the
- * budget; HZ_ERR_ARG for a malformed request.
+ * Queue `count` requests as one submission and return at once with a ticket.
+ * Submissions are admitted in order against the context's device-memory
+ * budget (each request's src_len + dst_cap, plus per-request scratch).  The
+ * context runs up to three device batches at once, each on its own stream as
+ * one CUDA graph with one persistent kernel per phase over all its requests;
+ * when a batch slot frees up, it takes every queued submission that fits the
+ * budget and HZ_OPT_BATCH_MAX_REQS (continuous batching).  HZ_ERR_BUSY if the
+ * submission alone exceeds the budget; HZ_ERR_ARG for a malformed request
+ * (unknown op, NULL pointer, src_len >= 2^32, block_size > 2^24, d_dst not
+ * 4-byte aligned, or a decompress d_src not 4-byte aligned).  The caller keeps
+ * every buffer alive and untouched until the ticket completes.
  */
 hz_status hz_submit(hz_ctx* ctx, const hz_request* reqs, uint32_t count, uint64_t* ticket_out);
 
@@ -263,6 +272,41 @@ hz_status hz_submit(hz_ctx* ctx, const hz_request* reqs, uint32_t count, uint64_
  */
 hz_status hz_poll(hz_ctx* ctx, uint64_t ticket, int64_t timeout_ns, hz_status* per_req,
                   uint64_t* out_lens);
+
+/*
+ * Request replay (the serving loop): an open-loop client over the batcher.
+ * Item i is submitted alone at items[i].arrival_s seconds after the call
+ * starts (items sorted by arrival_s); the batcher merges whatever is queued
+ * when a slot frees up (see hz_submit).  An item whose req.d_dst is NULL
+ * takes req.dst_cap bytes of the device ring d_ring[0..ring_bytes) (256-byte
+ * aligned, owned by the caller) from submission to completion, and waits for
+ * room when the ring is full.  Blocks until every item has completed; then
+ * records[i] (host array of `count`) holds its times (seconds from the
+ * start: handed to the batcher, completion seen on the host), status, result
+ * length, the device batch that carried it and its ring offset (~0 for items
+ * with their own d_dst; ring results are overwritten by later items).
+ * *wall_s (may be NULL) = start to the last completion.  HZ_ERR_ARG for
+ * unsorted items, a NULL d_dst without a usable ring, or a dst_cap larger
+ * than the ring.  Per-item errors go to records[i].status.
+ */
+typedef struct {
+  double arrival_s;
+  hz_request req;
+} hz_serve_item;
+
+typedef struct {
+  double submit_s;
+  double done_s;
+  uint64_t out_len;
+  uint64_t launch;
+  uint64_t dst_offset;
+  int32_t status;
+  uint32_t pad;
+} hz_serve_record;
+
+hz_status hz_serve_replay(hz_ctx* ctx, const hz_serve_item* items, uint64_t count,
+                          uint8_t* d_ring, uint64_t ring_bytes, hz_serve_record* records,
+                          double* wall_s);
 
 #ifdef __cplusplus
 }

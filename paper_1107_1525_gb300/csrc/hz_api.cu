@@ -219,6 +219,9 @@ hz_status hz_set_option(hz_ctx* c, int key, int64_t v) {
       if (v != 0 && v != 1) return HZ_ERR_ARG;
       hz_batch_set_plain(c->batch, v != 0);
       return HZ_OK;
+    case HZ_OPT_BATCH_MAX_REQS:
+      if (v < 1 || v > (1 << 20)) return HZ_ERR_ARG;
+      return hz_batch_set_max_reqs(c->batch, (uint32_t)v);
     default:
       return HZ_ERR_ARG;
   }
@@ -233,6 +236,7 @@ int64_t hz_get_option(hz_ctx* c, int key) {
     case HZ_OPT_DECODE_THREADS: return c->opt_dec_threads;
     case HZ_OPT_AUTOTUNE: return c->opt_autotune;
     case HZ_OPT_BATCH_PLAIN: return hz_batch_plain(c->batch) ? 1 : 0;
+    case HZ_OPT_BATCH_MAX_REQS: return hz_batch_max_reqs(c->batch);
     default: return -1;
   }
 }
@@ -508,3 +512,5 @@ void hz_ctx_get_tuned(hz_ctx* c, uint32_t* B, int* lut_bits) {
   *lut_bits = c->opt_lut_bits;
 }
 int hz_ctx_device(hz_ctx* c) { return c->device; }
+int hz_ctx_lut_bits(hz_ctx* c) { return c->opt_lut_bits; }
+BatchState* hz_ctx_batch(hz_ctx* c) { return c->batch; }

@@ -1,6 +1,9 @@
-// hz_batch.h -- batch submission and admission behind hz_submit / hz_poll.
+// hz_batch.h -- batch submission and admission behind hz_submit / hz_poll,
+// and the hooks the request-replay loop (hz_serve.cu) drives it through.
 #pragma once
 #include <stdint.h>
+
+#include <vector>
 
 #include "hz.h"
 
@@ -17,3 +20,16 @@ uint32_t hz_batch_tuned_block_size(uint64_t n);
 // Plain mode: requests run one after another through hz_compress / hz_decompress.
 void hz_batch_set_plain(BatchState* b, bool plain);
 bool hz_batch_plain(BatchState* b);
+// Most requests one device batch takes when queued submissions merge.
+hz_status hz_batch_set_max_reqs(BatchState* b, uint32_t m);
+uint32_t hz_batch_max_reqs(BatchState* b);
+
+// Retire finished launches and launch what the slots and budget allow.
+void hz_batch_progress(BatchState* b);
+// While on, every completed ticket is recorded; drain moves them to `out`.
+void hz_batch_track_finished(BatchState* b, bool on);
+void hz_batch_drain_finished(BatchState* b, std::vector<uint64_t>& out);
+// Non-blocking hz_poll that also reports the device batch that carried the
+// ticket and the host steady-clock time (ns) at which its completion was seen.
+hz_status hz_batch_take(BatchState* b, uint64_t ticket, hz_status* per_req, uint64_t* out_lens,
+                        uint64_t* launch_id, int64_t* done_ns);

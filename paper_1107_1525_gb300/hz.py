@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "HZ_OK", 1: "HZ_PENDING", -1: "HZ_ERR_ARG", -2: "HZ_ERR_CAPAC
 HEADER_BYTES = 280
 HZ_OPT_INDEX, HZ_OPT_PROFILE, HZ_OPT_DECODE_LUT_BITS = 1, 2, 3
 HZ_OPT_DECODE_THREADS, HZ_OPT_AUTOTUNE, HZ_OPT_BATCH_PLAIN = 4, 5, 6
+HZ_OPT_BATCH_MAX_REQS = 7
 HZ_OP_COMPRESS, HZ_OP_DECOMPRESS = 0, 1
 
 # the C symbols include/hz.h declares (checked by the test suite)
@@ -31,7 +32,7 @@ EXPORTS = ("hz_create", "hz_destroy", "hz_compress_bound", "hz_build_codes", "hz
            "hz_decompress", "hz_sync", "hz_compress_host", "hz_decompress_host",
            "hz_set_option", "hz_get_option", "hz_launch_count", "hz_profile_read",
            "hz_kernel_name", "hz_submit", "hz_poll", "hz_compress_noalloc", "hz_autotune",
-           "hz_tuned_block_size")
+           "hz_tuned_block_size", "hz_serve_replay")
 
 
 class HzError(RuntimeError):
@@ -49,6 +50,14 @@ class HzRequest(ctypes.Structure):
                 ("d_src", ctypes.c_void_p), ("src_len", ctypes.c_uint64),
                 ("d_dst", ctypes.c_void_p), ("dst_cap", ctypes.c_uint64)]
 
+
+# hz_serve_item / hz_serve_record as numpy record types (same layout as the C structs)
+SERVE_ITEM = np.dtype([("arrival_s", "<f8"), ("op", "<i4"), ("block_size", "<u4"),
+                       ("d_src", "<u8"), ("src_len", "<u8"), ("d_dst", "<u8"),
+                       ("dst_cap", "<u8")])
+SERVE_RECORD = np.dtype([("submit_s", "<f8"), ("done_s", "<f8"), ("out_len", "<u8"),
+                         ("launch", "<u8"), ("dst_offset", "<u8"), ("status", "<i4"),
+                         ("pad", "<u4")])
 
 _lib = None
 
@@ -83,6 +92,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hz_compress_noalloc": (i32, [vp, u64, u32, vp, u64, vp, vp, vp]),
         "hz_autotune": (i32, [vp, vp, u64, vp]),
         "hz_tuned_block_size": (u32, [vp, u64]),
+        "hz_serve_replay": (i32, [vp, vp, u64, vp, u64, vp, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -255,6 +265,21 @@ def hz_poll(ctx: Context, ticket: int, count: int, timeout_ns: int = -1):
     lens = np.zeros(max(1, count), dtype=np.uint64)
     st = ctx._lib.hz_poll(ctx.handle, ticket, timeout_ns, per.ctypes.data, lens.ctypes.data)
     return int(st), per[:count], lens[:count]
+
+
+def hz_serve_replay(ctx: Context, items: np.ndarray, ring=None, ring_bytes: int | None = None):
+    """Replay `items` (a SERVE_ITEM array sorted by arrival_s; d_dst 0 = use the
+    ring) open-loop; returns (SERVE_RECORD array, wall seconds)."""
+    items = np.ascontiguousarray(items, dtype=SERVE_ITEM)
+    rec = np.zeros(len(items), dtype=SERVE_RECORD)
+    wall = ctypes.c_double(0.0)
+    if ring_bytes is None:
+        ring_bytes = ring.numel() if ring is not None else 0
+    _check(ctx._lib.hz_serve_replay(ctx.handle, items.ctypes.data if len(items) else None,
+                                    len(items), _ptr(ring), ring_bytes,
+                                    rec.ctypes.data if len(items) else None, ctypes.byref(wall)),
+           "hz_serve_replay")
+    return rec, float(wall.value)
 
 
 # ------------------------------------------------ tensor-level conveniences
