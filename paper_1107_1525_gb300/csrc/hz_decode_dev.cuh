@@ -290,10 +290,10 @@ static __device__ __forceinline__ bool fast_capable(uint32_t B, uint32_t nw) {
 
 // Per lane, a ring of kRingSlots slots of 32 bytes of its payload range in
 // shared memory, fed by cp.async.  Refills happen at warp-uniform points,
-// every kRefillSteps decode steps: each lane keeps the three slots after the
-// one it is reading requested, and makes sure the next one has landed.  A
-// step advances at most W <= 12 bits, so kRefillSteps steps stay within two
-// slots and the window refills in between are plain shared-memory reads.
+// every kRefillSteps decode steps: each lane keeps the slots after the one it
+// is reading requested, and makes sure the next one has landed.  A step
+// advances at most W <= 12 bits, so kRefillSteps steps read at most six words
+// and the window fills in between are plain shared-memory reads.
 constexpr uint32_t kSlotWords = 8;
 constexpr uint32_t kRingSlots = 4;
 constexpr uint32_t kRingWords = kSlotWords * kRingSlots;
@@ -319,8 +319,13 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// 64-bit window over the payload, refilled from the lane's ring.  Words are
-// indexed from the 16-byte-aligned address at or below the payload start.
+// The lane's bit reader: a 64-bit buffer (bh:bl) holding the next nb payload
+// bits left-aligned (bits below them are zero), topped up one word at a time
+// from the lane's ring.  Peeking W bits is one shift and consuming l <= 31
+// bits is a funnel shift and a shift; fill() adds a word when nb <= 32, so
+// after it nb > 32 and two steps of at most 12 bits can follow before the
+// next fill.  Words are indexed from the 16-byte-aligned address at or below
+// the payload start.
 struct RingWin {
   const uint8_t* abase;  // 16-byte aligned base of the payload's slots
   uint32_t full_slots;   // slots [0, full_slots) lie wholly inside the stream buffer
@@ -328,9 +333,9 @@ struct RingWin {
   const uint32_t* ring;  // my ring (generic pointer into shared memory)
   uint32_t ring_s;       // my ring (shared-memory address)
   uint32_t off_w;        // payload word 0 = aligned word off_w
-  uint32_t A;            // aligned word index of w0
   uint32_t next_slot;    // next slot index (absolute) to request
-  uint32_t w0, w1;
+  uint32_t rw;           // next aligned word to move into the buffer
+  uint32_t bh, bl, nb;
   __device__ __forceinline__ void setup(const uint8_t* payload, const uint8_t* gend,
                                         const uint32_t* my_ring) {
     abase = reinterpret_cast<const uint8_t*>(((uintptr_t)payload) & ~(uintptr_t)15);
@@ -353,30 +358,46 @@ struct RingWin {
   // start at payload bit `pos` (waits for the first two slots)
   __device__ __forceinline__ void init(uint32_t pos) {
     cp_async_wait<0>();
-    A = off_w + (pos >> 5);
+    const uint32_t A = off_w + (pos >> 5);
     const uint32_t h0 = A / kSlotWords;
     request(h0);
     request(h0 + 1);
     request(h0 + 2);
     next_slot = h0 + 3;
     cp_async_wait<1>();
-    w0 = ring[A % kRingWords];
-    w1 = ring[(A + 1) % kRingWords];
+    const uint32_t w0 = ring[A % kRingWords], w1 = ring[(A + 1) % kRingWords];
+    const uint32_t r = pos & 31u;
+    bh = __funnelshift_l(w1, w0, r);
+    bl = w1 << r;
+    nb = 64u - r;
+    rw = A + 2;
   }
-  // warp-uniform refill point (see above)
+  // warp-uniform refill point: the words the next kRefillSteps steps can read
+  // (at most 6, from word rw on) are in slots rw / 8 and the one after; keep
+  // two more requested
   __device__ __forceinline__ void refill() {
-    const uint32_t cur = (A + 1) / kSlotWords;
+    const uint32_t cur = rw / kSlotWords;
     while (next_slot <= cur + 3) request(next_slot++);
     cp_async_wait<2>();
   }
-  __device__ __forceinline__ uint32_t peek(uint32_t pos) const { return __funnelshift_l(w1, w0, pos); }
-  // after an advance of at most 32 bits
-  __device__ __forceinline__ void cross(uint32_t pos) {
-    if (off_w + (pos >> 5) != A) {
-      ++A;
-      w0 = w1;
-      w1 = ring[(A + 1) % kRingWords];
+  __device__ __forceinline__ void fill() {
+    if (nb <= 32u) {
+      const uint32_t w = ring[rw % kRingWords];
+      const uint32_t s = 32u - nb;
+      uint32_t lo;
+      asm("shl.b32 %0, %1, %2;" : "=r"(lo) : "r"(w), "r"(s));  // 0 for s = 32
+      bh |= __funnelshift_lc(w, 0u, s);
+      bl |= lo;
+      nb += 32u;
+      ++rw;
     }
+  }
+  __device__ __forceinline__ uint32_t peek(uint32_t W) const { return bh >> (32u - W); }
+  // l <= 31 (a step of at most W bits)
+  __device__ __forceinline__ void consume(uint32_t l) {
+    bh = __funnelshift_l(bl, bh, l);
+    bl <<= l;
+    nb -= l;
   }
 };
 
@@ -434,34 +455,34 @@ static __device__ __forceinline__ uint32_t take_symbol(const FastShared& sh, GWi
   return ls & 0xFFu;
 }
 
-// One symbol from the ring window: length << 8 | symbol (0 when no code matches).
+// Decode one symbol from the ring window and advance; the window holds at
+// least W bits.  A long code, read straight from memory, restarts the window
+// (which waits for the ring and leaves it full) -- never the case for kSimple
+// codes.
 template <bool kSimple>
-__device__ __forceinline__ uint32_t ring_symbol(const FastShared& sh, const RingWin& w,
-                                                uint32_t pos, uint32_t W, const GWin& g) {
-  const uint32_t e = sh.lut[w.peek(pos) >> (32 - W)];
+__device__ __forceinline__ uint32_t ring_step(const FastShared& sh, RingWin& w, uint32_t& pos,
+                                              uint32_t W, const GWin& g, bool& bad) {
+  const uint32_t e = sh.lut[w.peek(W)];
   const uint32_t l0 = e_l0(e);
-  if (kSimple || l0) return (l0 << 8) | (e & 0xFFu);
-  return decode_long(sh.c, g.peek64_at(pos));
+  if (kSimple || l0) {
+    pos += l0;
+    w.consume(l0);
+    return e & 0xFFu;
+  }
+  const uint32_t ls = decode_long(sh.c, g.peek64_at(pos));
+  const uint32_t l = ls >> 8;
+  bad |= l == 0;
+  pos += l ? l : 1u;
+  w.init(pos);
+  return ls & 0xFFu;
 }
 
-// Decode one symbol and advance.  A long code restarts the window (which
-// waits for the ring) -- never the case for kSimple codes.
+// The same, filling the window first.
 template <bool kSimple>
 __device__ __forceinline__ uint32_t ring_take(const FastShared& sh, RingWin& w, uint32_t& pos,
                                               uint32_t W, const GWin& g, bool& bad) {
-  const uint32_t ls = ring_symbol<kSimple>(sh, w, pos, W, g);
-  const uint32_t l = ls >> 8;
-  if (kSimple) {
-    pos += l;
-    w.cross(pos);
-  } else {
-    bad |= l == 0;
-    const uint32_t adv = l ? l : 1u;
-    pos += adv;
-    if (adv <= 12) w.cross(pos);
-    else w.init(pos);
-  }
-  return ls & 0xFFu;
+  w.fill();
+  return ring_step<kSimple>(sh, w, pos, W, g, bad);
 }
 
 template <bool kSimple>
@@ -501,20 +522,25 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
     bool dummy = false;
     while (__any_sync(0xFFFFFFFFu, active && pos + W <= my_end)) {
       if (active) w.refill();
-#pragma unroll 4
-      for (uint32_t s = 0; s < kRefillSteps; ++s) {
-        if (active && pos + W <= my_end) {
-          const uint32_t e = sh.lut[w.peek(pos) >> (32 - W)];
-          const uint32_t ns = e_ns(e);
-          if (!kSimple && ns == 0) {  // a long code, or no code at all on a wrong path
-            const uint32_t l = decode_long(sh.c, g.peek64_at(pos)) >> 8;
-            pos += l ? l : 1u;
-            ++c;
-            w.init(pos);
-          } else {
-            pos += e_nbits(e);
-            c += ns;
-            w.cross(pos);
+#pragma unroll 2
+      for (uint32_t s = 0; s < kRefillSteps; s += 2) {
+        w.fill();  // two steps of at most W <= 12 bits follow
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          if (active && pos + W <= my_end) {
+            const uint32_t e = sh.lut[w.peek(W)];
+            const uint32_t ns = e_ns(e);
+            if (!kSimple && ns == 0) {  // a long code, or no code at all on a wrong path
+              const uint32_t l = decode_long(sh.c, g.peek64_at(pos)) >> 8;
+              pos += l ? l : 1u;
+              ++c;
+              w.init(pos);
+            } else {
+              const uint32_t nbits = e_nbits(e);
+              pos += nbits;
+              c += ns;
+              w.consume(nbits);
+            }
           }
         }
       }
@@ -596,7 +622,10 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
         for (int j = 0; j < 4; ++j) {
           uint32_t word = 0;
 #pragma unroll
-          for (int b = 0; b < 4; ++b) word |= ring_take<kSimple>(sh, w, pos, W, g, bad) << (8 * b);
+          for (int b = 0; b < 4; ++b) {
+            if ((b & 1) == 0) w.fill();  // two steps of at most W <= 12 bits follow
+            word |= ring_step<kSimple>(sh, w, pos, W, g, bad) << (8 * b);
+          }
           q[j] = word;
         }
         *reinterpret_cast<uint4*>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
