@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kFastThreads) batch_decode_kernel(BatchCtl* ct
   __shared__ uint32_t s_u;
   const uint32_t nunits = ctl->dec_units, n = ctl->ndecomp;
   uint32_t cur = 0xFFFFFFFFu;
-  bool simple = false;
+  int mode = 2;
   for (;;) {
     const uint32_t u = take_ticket(&ctl->tickets[kTicketDecode], &s_u);
     if (u >= nunits) break;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kFastThreads) batch_decode_kernel(BatchCtl* ct
       load_canon(sh.c, T, threadIdx.x, kFastThreads);
       cur = i;
       __syncthreads();
-      simple = T->complete && sh.c.maxlen <= sh.c.W;
+      mode = fast_mode(T, sh.c);
     }
     const DecodeArgs a = decomp_args(d);
     const uint32_t warp = threadIdx.x >> 5;
@@ -245,8 +245,7 @@ __global__ void __launch_bounds__(kFastThreads) batch_decode_kernel(BatchCtl* ct
     for (uint32_t j = 0; j < d.per_warp; ++j) {
       const uint32_t k = k0 + j;
       if (k >= sh.c.nb) break;
-      if (simple) decode_block_warp<true>(a, sh, k);
-      else decode_block_warp<false>(a, sh, k);
+      decode_block_fast(a, sh, k, mode);
     }
   }
 }

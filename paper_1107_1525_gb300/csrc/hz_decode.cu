@@ -51,12 +51,9 @@ __global__ void __launch_bounds__(kFastThreads) decode_fast_kernel(DecodeArgs a,
   __syncthreads();
   const uint32_t warps = kFastThreads / 32;
   const uint32_t stride = gridDim.x * warps;
-  // every code fits the table and every table value decodes: no escapes
-  const bool simple = T->complete && sh.c.maxlen <= sh.c.W;
-  for (uint32_t k = blockIdx.x * warps + (threadIdx.x >> 5); k < sh.c.nb; k += stride) {
-    if (simple) decode_block_warp<true>(a, sh, k);
-    else decode_block_warp<false>(a, sh, k);
-  }
+  const int mode = fast_mode(T, sh.c);
+  for (uint32_t k = blockIdx.x * warps + (threadIdx.x >> 5); k < sh.c.nb; k += stride)
+    decode_block_fast(a, sh, k, mode);
 }
 
 template <int NT>

@@ -399,7 +399,24 @@ struct RingWin {
     bl <<= l;
     nb -= l;
   }
+  // the buffer as 64 bits, MSB first (valid for the next nb bits)
+  __device__ __forceinline__ uint64_t peek64() const { return ((uint64_t)bh << 32) | bl; }
+  // l <= 32 <= nb (a code of up to 32 bits, right after a fill)
+  __device__ __forceinline__ void consume_long(uint32_t l) {
+    uint32_t lo;
+    asm("shl.b32 %0, %1, %2;" : "=r"(lo) : "r"(bl), "r"(l));  // 0 for l = 32
+    bh = __funnelshift_lc(bl, bh, l);
+    bl = lo;
+    nb -= l;
+  }
 };
+
+// How the fast decoder reads codes: kMode 0 -- the code is complete and no
+// code is longer than the table width W, so every table entry resolves at
+// least one symbol; kMode 1 -- codes of up to 32 bits: a longer code is
+// decoded from the window itself (filled before every step, so it holds more
+// than 32 bits); kMode 2 -- any length: a longer code is read straight from
+// memory and restarts the window.
 
 // 64-bit window over the payload words read straight from global memory
 // (through L1), refilled one word at a time: the fix-up's short walks and
@@ -456,18 +473,27 @@ static __device__ __forceinline__ uint32_t take_symbol(const FastShared& sh, GWi
 }
 
 // Decode one symbol from the ring window and advance; the window holds at
-// least W bits.  A long code, read straight from memory, restarts the window
-// (which waits for the ring and leaves it full) -- never the case for kSimple
-// codes.
-template <bool kSimple>
+// least W bits (more than 32 for kMode 1).  In kMode 2 a long code, read
+// straight from memory, restarts the window (which waits for the ring and
+// leaves it full).
+template <int kMode>
 __device__ __forceinline__ uint32_t ring_step(const FastShared& sh, RingWin& w, uint32_t& pos,
                                               uint32_t W, const GWin& g, bool& bad) {
   const uint32_t e = sh.lut[w.peek(W)];
   const uint32_t l0 = e_l0(e);
-  if (kSimple || l0) {
+  if (kMode == 0 || l0) {
     pos += l0;
     w.consume(l0);
     return e & 0xFFu;
+  }
+  if (kMode == 1) {
+    const uint32_t ls = decode_long(sh.c, w.peek64());
+    const uint32_t l = ls >> 8;
+    bad |= l == 0;
+    const uint32_t adv = l ? l : 1u;
+    pos += adv;
+    w.consume_long(adv);
+    return ls & 0xFFu;
   }
   const uint32_t ls = decode_long(sh.c, g.peek64_at(pos));
   const uint32_t l = ls >> 8;
@@ -478,14 +504,14 @@ __device__ __forceinline__ uint32_t ring_step(const FastShared& sh, RingWin& w, 
 }
 
 // The same, filling the window first.
-template <bool kSimple>
+template <int kMode>
 __device__ __forceinline__ uint32_t ring_take(const FastShared& sh, RingWin& w, uint32_t& pos,
                                               uint32_t W, const GWin& g, bool& bad) {
   w.fill();
-  return ring_step<kSimple>(sh, w, pos, W, g, bad);
+  return ring_step<kMode>(sh, w, pos, W, g, bad);
 }
 
-template <bool kSimple>
+template <int kMode>
 __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t k) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t W = sh.c.W;
@@ -527,10 +553,17 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
         w.fill();  // two steps of at most W <= 12 bits follow
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
+          if (kMode == 1 && t == 1) w.fill();  // a long code needs more than 32 bits
           if (active && pos + W <= my_end) {
             const uint32_t e = sh.lut[w.peek(W)];
             const uint32_t ns = e_ns(e);
-            if (!kSimple && ns == 0) {  // a long code, or no code at all on a wrong path
+            if (kMode == 1 && ns == 0) {  // a long code, or no code at all on a wrong path
+              const uint32_t l = decode_long(sh.c, w.peek64()) >> 8;
+              const uint32_t adv = l ? l : 1u;
+              pos += adv;
+              ++c;
+              w.consume_long(adv);
+            } else if (kMode == 2 && ns == 0) {
               const uint32_t l = decode_long(sh.c, g.peek64_at(pos)) >> 8;
               pos += l ? l : 1u;
               ++c;
@@ -548,7 +581,7 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
     if (active) {
       w.refill();
       while (pos < my_end) {
-        ring_take<kSimple>(sh, w, pos, W, g, dummy);
+        ring_take<kMode>(sh, w, pos, W, g, dummy);
         ++c;
       }
       exit_ = pos;
@@ -609,7 +642,7 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
       w.init(pos);
       // bytes up to a 16-byte boundary (at most 15 steps: within the slots init awaited)
       while (rem && (((uintptr_t)dst) & 15)) {
-        *dst++ = (uint8_t)ring_take<kSimple>(sh, w, pos, W, g, bad);
+        *dst++ = (uint8_t)ring_take<kMode>(sh, w, pos, W, g, bad);
         --rem;
       }
     }
@@ -623,8 +656,8 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
           uint32_t word = 0;
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
-            if ((b & 1) == 0) w.fill();  // two steps of at most W <= 12 bits follow
-            word |= ring_step<kSimple>(sh, w, pos, W, g, bad) << (8 * b);
+            if (kMode != 0 || (b & 1) == 0) w.fill();  // kMode 0: two steps of <= 12 bits follow
+            word |= ring_step<kMode>(sh, w, pos, W, g, bad) << (8 * b);
           }
           q[j] = word;
         }
@@ -636,7 +669,7 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
     if (rem) {
       w.refill();
       while (rem) {
-        *dst++ = (uint8_t)ring_take<kSimple>(sh, w, pos, W, g, bad);
+        *dst++ = (uint8_t)ring_take<kMode>(sh, w, pos, W, g, bad);
         --rem;
       }
     }
@@ -644,6 +677,19 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
   }
   cp_async_wait<0>();  // nothing of this block may land in the ring after we leave
   if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x322);
+}
+
+// The decoder mode for the tables (see RingWin), and one block in that mode.
+static __device__ __forceinline__ int fast_mode(const DecTables* T, const CanonTables& c) {
+  if (T->complete && c.maxlen <= c.W) return 0;  // every code fits the table: no escapes
+  return c.maxlen <= 32 ? 1 : 2;
+}
+
+static __device__ __forceinline__ void decode_block_fast(const DecodeArgs& a, FastShared& sh,
+                                                         uint32_t k, int mode) {
+  if (mode == 0) decode_block_warp<0>(a, sh, k);
+  else if (mode == 1) decode_block_warp<1>(a, sh, k);
+  else decode_block_warp<2>(a, sh, k);
 }
 
 // ================================================================ generic kernel
