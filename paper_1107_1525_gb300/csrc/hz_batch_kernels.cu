@@ -232,9 +232,7 @@ __global__ void __launch_bounds__(kFastThreads) batch_decode_kernel(BatchCtl* ct
     const BatchDecomp& d = decomps[i];
     const DecTables* T = d.T;
     if (i != cur) {
-      const int W = (int)T->lut_bits;
-      for (int k = threadIdx.x; k < (1 << W); k += kFastThreads) sh.lut[k] = T->lut[k];
-      load_canon(sh.c, T, threadIdx.x, kFastThreads);
+      load_fast_tables(sh, T, threadIdx.x, kFastThreads);
       cur = i;
       __syncthreads();
       mode = fast_mode(T, sh.c);

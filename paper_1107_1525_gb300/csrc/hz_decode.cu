@@ -45,9 +45,7 @@ __global__ void __launch_bounds__(kFastThreads) decode_fast_kernel(DecodeArgs a,
   __shared__ FastShared sh;
   if (!T->ok) return;
   if (!fast_block_size(T->B)) return;  // every block goes to the generic kernel
-  const int W = (int)T->lut_bits;
-  for (int i = threadIdx.x; i < (1 << W); i += kFastThreads) sh.lut[i] = T->lut[i];
-  load_canon(sh.c, T, threadIdx.x, kFastThreads);
+  load_fast_tables(sh, T, threadIdx.x, kFastThreads);
   __syncthreads();
   const uint32_t warps = kFastThreads / 32;
   const uint32_t stride = gridDim.x * warps;

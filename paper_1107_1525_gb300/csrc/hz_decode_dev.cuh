@@ -8,10 +8,14 @@
 namespace hz {
 
 // Lookup-table entry for the W-bit value v (u32):
-//   bits  0..7   first symbol            bits  8..15  second symbol
+//   bits  0..7   first symbol            bits  8..15  second symbol (0 if none)
 //   bits 16..17  symbols resolved (0: the first code is longer than W bits,
 //                or no code matches), 1 or 2
 //   bits 18..22  bits consumed by them   bits 23..26  length of the first code
+// When no symbol resolves and the second-level table exists, a value that
+// starts codes longer than W bits holds instead, in bits 0..15, the start of
+// its part of the second-level table and, in bits 18..22, the e >= 1 extra
+// bits that index it; an all-zero entry means no code starts with v.
 static __host__ __device__ constexpr uint32_t lut_entry(uint32_t s0, uint32_t s1, uint32_t ns,
                                                  uint32_t nbits, uint32_t l0) {
   return s0 | (s1 << 8) | (ns << 16) | (nbits << 18) | (l0 << 23);
@@ -19,6 +23,11 @@ static __host__ __device__ constexpr uint32_t lut_entry(uint32_t s0, uint32_t s1
 static __device__ __forceinline__ uint32_t e_ns(uint32_t e) { return (e >> 16) & 3u; }
 static __device__ __forceinline__ uint32_t e_nbits(uint32_t e) { return (e >> 18) & 31u; }
 static __device__ __forceinline__ uint32_t e_l0(uint32_t e) { return (e >> 23) & 15u; }
+
+// Second-level table entries: codes longer than W bits whose W-bit prefixes
+// have at most this many continuations in all; larger code sets take the
+// per-length search.
+constexpr uint32_t kL2Entries = 2048;
 
 struct DecTables {
   uint32_t ok;          // 1 once the header has been checked
@@ -32,6 +41,8 @@ struct DecTables {
   uint64_t first[kMaxLen + 1];  // first canonical code of each length
   uint8_t sorted[256];          // symbols in (length, byte) order
   uint32_t lut[1 << kLutMaxBits];
+  uint32_t has_l2;              // the second-level table below is built
+  uint16_t l2[kL2Entries];      // symbol | length << 8 of codes longer than W (0: none)
 };
 
 
@@ -138,17 +149,78 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
     }
     return 0;
   };
-  for (uint32_t v = t; v < (1u << W); v += blockDim.x) {
+  // each thread takes a run of consecutive values, so that the second-level
+  // parts can be laid out in value order by one scan
+  __shared__ uint8_t s_ext[1 << kLutMaxBits];     // extra bits of an escape value, else 0
+  __shared__ uint16_t s_base[1 << kLutMaxBits];   // its first second-level entry
+  __shared__ uint32_t s_part[256];
+  __shared__ uint32_t s_l2_total;
+  const uint32_t nv = 1u << W, per = (nv + blockDim.x - 1) / blockDim.x;
+  uint32_t my_l2 = 0;
+  for (uint32_t v = t * per; v < (t + 1) * per && v < nv; ++v) {
     uint32_t s0 = 0, s1 = 0;
     const uint32_t l0 = code_at(v, W, s0);
-    uint32_t e = 0;
+    uint32_t e = 0, ext = 0;
     if (l0) {
       const uint32_t rest = W - l0;
       const uint32_t l1 = rest ? code_at(v & ((1u << rest) - 1u), (int)rest, s1) : 0u;
       e = l1 ? lut_entry(s0, s1, 2, l0 + l1, l0) : lut_entry(s0, 0, 1, l0, l0);
+    } else {
+      // the longest code (of up to 32 bits) that starts with v
+      for (uint32_t k = (uint32_t)W + 1; k <= maxl && k <= 32; ++k) {
+        if (!cnt[k]) continue;
+        const uint64_t lo_p = first[k] >> (k - W), hi_p = (first[k] + cnt[k] - 1) >> (k - W);
+        if (v >= lo_p && v <= hi_p) ext = k - (uint32_t)W;
+      }
+      my_l2 += ext ? (1u << ext) : 0u;
     }
+    s_ext[v] = (uint8_t)ext;
     T->lut[v] = e;
   }
+  s_part[t] = my_l2;
+  __syncthreads();
+  if (t == 0) {
+    uint32_t acc = 0;
+    for (uint32_t i = 0; i < blockDim.x; ++i) {
+      const uint32_t c2 = s_part[i];
+      s_part[i] = acc;
+      acc += c2;
+    }
+    s_l2_total = acc;
+  }
+  __syncthreads();
+  const uint32_t l2_total = s_l2_total;
+  const bool l2_ok = maxl <= 32 && l2_total <= kL2Entries;
+  {
+    uint32_t at = s_part[t];
+    for (uint32_t v = t * per; v < (t + 1) * per && v < nv; ++v) {
+      const uint32_t ext = s_ext[v];
+      s_base[v] = (uint16_t)(l2_ok ? at : 0u);
+      if (ext && l2_ok) {
+        T->lut[v] = at | (ext << 18);
+        at += 1u << ext;
+      }
+    }
+  }
+  __syncthreads();
+  if (l2_ok) {
+    // entry i belongs to the escape value with the last base <= i
+    for (uint32_t i = t; i < l2_total; i += blockDim.x) {
+      uint32_t lo_v = 0, hi_v = nv;  // last v with s_base[v] <= i
+      while (hi_v - lo_v > 1) {
+        const uint32_t mid = (lo_v + hi_v) >> 1;
+        if (s_base[mid] <= i) lo_v = mid;
+        else hi_v = mid;
+      }
+      while (lo_v > 0 && s_ext[lo_v] == 0) --lo_v;  // values without a part share the next base
+      const uint32_t ext = s_ext[lo_v];
+      const uint32_t u = (lo_v << ext) | (i - s_base[lo_v]);
+      uint32_t sym = 0;
+      const uint32_t k = code_at(u, W + (int)ext, sym);
+      T->l2[i] = k ? (uint16_t)(sym | (k << 8)) : (uint16_t)0;
+    }
+  }
+  if (t == 0) T->has_l2 = l2_ok ? 1u : 0u;
   const bool cap_ok = n <= a.out_cap;
   if (t == 0) {
     T->flags = flags;
@@ -302,9 +374,26 @@ constexpr uint32_t kRefillSteps = 16;
 
 struct FastShared {
   uint32_t lut[1 << kLutMaxBits];
+  uint16_t l2[kL2Entries];
+  uint32_t has_l2;
   CanonTables c;
   __align__(16) uint32_t ring[kFastThreads * kRingStride];
 };
+
+// The lookup tables of T into shared memory (all threads of the CTA).
+static __device__ __forceinline__ void load_fast_tables(FastShared& sh, const DecTables* T,
+                                                        int tid, int nt) {
+  const int W = (int)T->lut_bits;
+  for (int i = tid; i < (1 << W); i += nt) sh.lut[i] = T->lut[i];
+  const uint32_t has_l2 = T->has_l2;
+  if (has_l2) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(T->l2);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(sh.l2);
+    for (int i = tid; i < (int)(kL2Entries / 2); i += nt) dst[i] = src[i];
+  }
+  if (tid == 0) sh.has_l2 = has_l2;
+  load_canon(sh.c, T, tid, nt);
+}
 
 static __device__ __forceinline__ void cp_async16(uint32_t smem_addr, const void* gptr, uint32_t bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr), "l"(gptr),
@@ -415,8 +504,9 @@ struct RingWin {
 // code is longer than the table width W, so every table entry resolves at
 // least one symbol; kMode 1 -- codes of up to 32 bits: a longer code is
 // decoded from the window itself (filled before every step, so it holds more
-// than 32 bits); kMode 2 -- any length: a longer code is read straight from
-// memory and restarts the window.
+// than 32 bits), through the second-level table when there is one; kMode 2 --
+// any length: a longer code is read straight from memory and restarts the
+// window.
 
 // 64-bit window over the payload words read straight from global memory
 // (through L1), refilled one word at a time: the fix-up's short walks and
@@ -472,6 +562,18 @@ static __device__ __forceinline__ uint32_t take_symbol(const FastShared& sh, GWi
   return ls & 0xFFu;
 }
 
+// A code longer than W bits (kMode 1) from the window's first 64 bits, given
+// its table entry e: length << 8 | symbol, 0 when no code matches.
+static __device__ __forceinline__ uint32_t long_code(const FastShared& sh, uint32_t e,
+                                                     uint64_t v64, uint32_t W) {
+  if (sh.has_l2) {
+    const uint32_t ext = e_nbits(e);
+    if (!ext) return 0u;  // no code starts with these W bits
+    return sh.l2[(e & 0xFFFFu) + (uint32_t)((v64 << W) >> (64 - ext))];
+  }
+  return decode_long(sh.c, v64);
+}
+
 // Decode one symbol from the ring window and advance; the window holds at
 // least W bits (more than 32 for kMode 1).  In kMode 2 a long code, read
 // straight from memory, restarts the window (which waits for the ring and
@@ -487,7 +589,7 @@ __device__ __forceinline__ uint32_t ring_step(const FastShared& sh, RingWin& w, 
     return e & 0xFFu;
   }
   if (kMode == 1) {
-    const uint32_t ls = decode_long(sh.c, w.peek64());
+    const uint32_t ls = long_code(sh, e, w.peek64(), W);
     const uint32_t l = ls >> 8;
     bad |= l == 0;
     const uint32_t adv = l ? l : 1u;
@@ -558,7 +660,7 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
             const uint32_t e = sh.lut[w.peek(W)];
             const uint32_t ns = e_ns(e);
             if (kMode == 1 && ns == 0) {  // a long code, or no code at all on a wrong path
-              const uint32_t l = decode_long(sh.c, w.peek64()) >> 8;
+              const uint32_t l = long_code(sh, e, w.peek64(), W) >> 8;
               const uint32_t adv = l ? l : 1u;
               pos += adv;
               ++c;
