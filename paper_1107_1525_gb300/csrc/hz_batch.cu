@@ -64,6 +64,7 @@ struct Slot {
   BatchDecomp* d_decomps = nullptr;
   BatchResult* d_results = nullptr;
   DevState* d_states = nullptr;
+  uint32_t* d_bases = nullptr;  // 3 x req_cap: histogram, tile and decode-unit bases
   DecTables* d_dec = nullptr;
   uint64_t* d_lens = nullptr;
   TileStatus* d_tiles = nullptr;
@@ -129,6 +130,7 @@ static void free_slot_buffers(Slot& s) {
   cudaFree(s.d_decomps);
   cudaFree(s.d_results);
   cudaFree(s.d_states);
+  cudaFree(s.d_bases);
   cudaFree(s.d_dec);
   cudaFree(s.d_lens);
   cudaFree(s.d_tiles);
@@ -141,6 +143,7 @@ static void free_slot_buffers(Slot& s) {
   s.d_decomps = nullptr;
   s.d_results = nullptr;
   s.d_states = nullptr;
+  s.d_bases = nullptr;
   s.d_dec = nullptr;
   s.d_lens = nullptr;
   s.d_tiles = nullptr;
@@ -173,6 +176,7 @@ static hz_status ensure_slot(BatchState* b, Slot& s, uint32_t reqs, uint64_t til
             cudaMalloc(&s.d_decomps, rc * sizeof(BatchDecomp)) == cudaSuccess &&
             cudaMalloc(&s.d_results, rc * sizeof(BatchResult)) == cudaSuccess &&
             cudaMalloc(&s.d_states, rc * sizeof(DevState)) == cudaSuccess &&
+            cudaMalloc(&s.d_bases, 3ull * rc * sizeof(uint32_t)) == cudaSuccess &&
             cudaMalloc(&s.d_dec, rc * batch_dec_tables_bytes()) == cudaSuccess &&
             cudaMalloc(&s.d_lens, rc * sizeof(uint64_t)) == cudaSuccess &&
             cudaMalloc(&s.d_tiles, tc * sizeof(TileStatus)) == cudaSuccess &&
@@ -407,6 +411,9 @@ static hz_status launch_batched(BatchState* b, const std::vector<Job*>& group, i
   ctl.ndecomp = nd;
   ctl.hist_units = hist_units;
   ctl.tiles = tile_base;
+  ctl.hist_base = s.d_bases;
+  ctl.tile_base = s.d_bases + s.req_cap;
+  ctl.unit_base = s.d_bases + 2ull * s.req_cap;
   *s.h_ctl = ctl;
   if (cudaGraphLaunch(s.graph, s.stream) != cudaSuccess ||
       cudaEventRecord(s.done, s.stream) != cudaSuccess) {

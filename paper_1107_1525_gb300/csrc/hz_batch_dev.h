@@ -17,6 +17,11 @@ struct BatchCtl {
   uint32_t dec_units;   // decode units, counted on the device
   uint32_t pad[3];
   uint32_t tickets[kTickets];
+  // first work unit of each request, as compact arrays (filled on the device)
+  // so that finding a unit's request searches a few cache lines
+  uint32_t* hist_base;  // [ncomp]
+  uint32_t* tile_base;  // [ncomp]
+  uint32_t* unit_base;  // [ndecomp]
 };
 
 struct BatchComp {

@@ -20,18 +20,37 @@
 
 namespace hz {
 
-// Index of the request whose [base, base + units) range holds unit u.
-template <class Item, class BaseF>
-__device__ __forceinline__ uint32_t find_item(const Item* items, uint32_t count, uint32_t u,
-                                              BaseF base) {
-  uint32_t lo = 0, hi = count;  // first item with base > u, minus one
+// Index of the request whose [base[i], base[i + 1]) range holds unit u
+// (bases ascending, base[0] = 0).
+__device__ __forceinline__ uint32_t find_item(const uint32_t* base, uint32_t count, uint32_t u) {
+  uint32_t lo = 0, hi = count;  // last i with base[i] <= u
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (base(items[mid]) <= u) lo = mid;
+    if (__ldg(base + mid) <= u) lo = mid;
     else hi = mid;
   }
   return lo;
 }
+
+// Encoder tiles are handed out in chunks of consecutive tiles, so that a CTA
+// mostly stays inside one request and loads its tables once per chunk.
+constexpr uint32_t kBatchTileChunk = 8;
+
+// The request that holds a unit, remembered across calls: a unit inside the
+// last request's range needs no search.  Works for any order of units.
+struct RequestCursor {
+  const uint32_t* base;
+  uint32_t count, total;
+  uint32_t i = 0xFFFFFFFFu, lo = 1, hi = 0;  // [lo, hi): units of request i
+  __device__ __forceinline__ uint32_t find(uint32_t u) {
+    if (u < lo || u >= hi) {
+      i = find_item(base, count, u);
+      lo = __ldg(base + i);
+      hi = i + 1 < count ? __ldg(base + i + 1) : total;
+    }
+    return i;
+  }
+};
 
 __device__ __forceinline__ EncodeArgs comp_args(const BatchComp& c) {
   EncodeArgs a;
@@ -64,12 +83,32 @@ __device__ __forceinline__ DecodeArgs decomp_args(const BatchDecomp& d) {
   return a;
 }
 
-__device__ __forceinline__ uint32_t take_ticket(uint32_t* counter, uint32_t* s_slot) {
-  __syncthreads();
-  if (threadIdx.x == 0) *s_slot = atomicAdd(counter, 1u);
-  __syncthreads();
-  return *s_slot;
-}
+// A CTA's stream of work units from a global ticket counter.  Thread 0 asks
+// for the next ticket as soon as it hands out the current one, so the atomic's
+// round trip overlaps the current unit's work instead of stalling the CTA.
+// Every thread of the CTA calls first() and next() (they hold barriers).
+struct TicketStream {
+  uint32_t* counter;
+  uint32_t* slot;  // shared: the current ticket
+  uint32_t ahead;  // thread 0: the ticket after it
+  __device__ __forceinline__ uint32_t first() {
+    if (threadIdx.x == 0) {
+      *slot = atomicAdd(counter, 1u);
+      ahead = atomicAdd(counter, 1u);
+    }
+    __syncthreads();
+    return *slot;
+  }
+  __device__ __forceinline__ uint32_t next() {
+    __syncthreads();  // every thread is done with the current unit
+    if (threadIdx.x == 0) {
+      *slot = ahead;
+      ahead = atomicAdd(counter, 1u);
+    }
+    __syncthreads();
+    return *slot;
+  }
+};
 
 // ------------------------------------------------------------- histogram
 __global__ void __launch_bounds__(kHistThreads) batch_hist_kernel(BatchCtl* ctl,
@@ -77,10 +116,9 @@ __global__ void __launch_bounds__(kHistThreads) batch_hist_kernel(BatchCtl* ctl,
   __shared__ uint32_t h[256 * 32];
   __shared__ uint32_t s_u;
   const uint32_t nunits = ctl->hist_units, ncomp = ctl->ncomp;
-  for (;;) {
-    const uint32_t u = take_ticket(&ctl->tickets[kTicketHist], &s_u);
-    if (u >= nunits) break;
-    const uint32_t i = find_item(comps, ncomp, u, [](const BatchComp& c) { return c.hist_base; });
+  TicketStream ts{&ctl->tickets[kTicketHist], &s_u, 0u};
+  for (uint32_t u = ts.first(); u < nunits; u = ts.next()) {
+    const uint32_t i = find_item(ctl->hist_base, ncomp, u);
     const BatchComp& c = comps[i];
     const uint64_t lo = (uint64_t)(u - c.hist_base) * kBatchHistChunk;
     const uint64_t len = c.n - lo < kBatchHistChunk ? c.n - lo : kBatchHistChunk;
@@ -110,21 +148,25 @@ __global__ void __launch_bounds__(kEncThreads) batch_summary_kernel(BatchCtl* ct
   __shared__ Summary s_warp[kEncThreads / 32];
   __shared__ uint32_t s_u;
   const uint32_t ntiles = ctl->tiles, ncomp = ctl->ncomp;
-  uint32_t cur = 0xFFFFFFFFu;
-  for (;;) {
-    const uint32_t u = take_ticket(&ctl->tickets[kTicketSummary], &s_u);
-    if (u >= ntiles) break;
-    const uint32_t i = find_item(comps, ncomp, u, [](const BatchComp& c) { return c.tile_base; });
-    const BatchComp& c = comps[i];
-    if (c.st->codes.maxlen > (uint32_t)kMaxLen) continue;  // code construction failed
-    if (i != cur) {
-      for (int s = threadIdx.x; s < 256; s += kEncThreads) s_len[s] = c.st->codes.len[s];
-      cur = i;
-      __syncthreads();
+  RequestCursor rc{ctl->tile_base, ncomp, ntiles};
+  uint32_t loaded = 0xFFFFFFFFu;  // the request whose lengths are in s_len
+  TicketStream ts{&ctl->tickets[kTicketSummary], &s_u, 0u};
+  for (uint32_t u = ts.first(); u * kBatchTileChunk < ntiles; u = ts.next()) {
+    const uint32_t t_end = min(u * kBatchTileChunk + kBatchTileChunk, ntiles);
+    for (uint32_t tile = u * kBatchTileChunk; tile < t_end; ++tile) {
+      const uint32_t i = rc.find(tile);
+      const BatchComp& c = comps[i];
+      if (c.st->codes.maxlen > (uint32_t)kMaxLen) continue;  // code construction failed
+      if (i != loaded) {
+        __syncthreads();  // nobody still reads the previous request's lengths
+        for (int s = threadIdx.x; s < 256; s += kEncThreads) s_len[s] = c.st->codes.len[s];
+        loaded = i;
+        __syncthreads();
+      }
+      bool bad = false;
+      summary_tile(comp_args(c), tile - c.tile_base, s_len, s_wsum, s_warp, bad);
+      if (bad) set_error(c.st, HZ_ERR_ARG, 0x200);
     }
-    bool bad = false;
-    summary_tile(comp_args(c), u - c.tile_base, s_len, s_wsum, s_warp, bad);
-    if (bad) set_error(c.st, HZ_ERR_ARG, 0x200);
   }
 }
 
@@ -148,20 +190,26 @@ __global__ void __launch_bounds__(kEncThreads, 3) batch_pack_kernel(BatchCtl* ct
   PackShared& sh = *reinterpret_cast<PackShared*>(smem_raw);
   __shared__ uint32_t s_u;
   const uint32_t ntiles = ctl->tiles, ncomp = ctl->ncomp;
-  uint32_t cur = 0xFFFFFFFFu, maxlen = 0;
-  for (;;) {
-    const uint32_t u = take_ticket(&ctl->tickets[kTicketPack], &s_u);
-    if (u >= ntiles) break;
-    const uint32_t i = find_item(comps, ncomp, u, [](const BatchComp& c) { return c.tile_base; });
-    const BatchComp& c = comps[i];
-    if (!c.st->enc_ok || c.st->error) continue;  // uniform: nothing to pack for this request
-    if (i != cur) {
-      pack_load_tables(sh, comp_args(c));
-      maxlen = c.st->codes.maxlen;
-      cur = i;
+  uint32_t maxlen = 0;
+  RequestCursor rc{ctl->tile_base, ncomp, ntiles};
+  uint32_t loaded = 0xFFFFFFFFu;  // the request whose tables are in sh
+  TicketStream ts{&ctl->tickets[kTicketPack], &s_u, 0u};
+  for (uint32_t u = ts.first(); u * kBatchTileChunk < ntiles; u = ts.next()) {
+    const uint32_t t_end = min(u * kBatchTileChunk + kBatchTileChunk, ntiles);
+    for (uint32_t tile = u * kBatchTileChunk; tile < t_end; ++tile) {
+      const uint32_t i = rc.find(tile);
+      const BatchComp& c = comps[i];
+      if (!c.st->enc_ok || c.st->error) continue;  // uniform: nothing to pack for this request
+      if (i != loaded) {
+        __syncthreads();  // nobody still reads the previous request's tables
+        pack_load_tables(sh, comp_args(c));
+        maxlen = c.st->codes.maxlen;
+        loaded = i;
+        __syncthreads();
+      }
+      pack_one_tile(sh, tile - c.tile_base, maxlen);
       __syncthreads();
     }
-    pack_one_tile(sh, u - c.tile_base, maxlen);
   }
 }
 
@@ -209,7 +257,10 @@ __global__ void __launch_bounds__(1024) batch_dscan_kernel(BatchCtl* ctl, BatchD
       tot += s_warp[w];
     }
     const uint32_t carry = s_carry;
-    if (i < n) decomps[i].unit_base = carry + wpre + inc - units;
+    if (i < n) {
+      decomps[i].unit_base = carry + wpre + inc - units;
+      ctl->unit_base[i] = carry + wpre + inc - units;
+    }
     __syncthreads();
     if (threadIdx.x == 0) s_carry = carry + tot;
   }
@@ -225,10 +276,9 @@ __global__ void __launch_bounds__(kFastThreads) batch_decode_kernel(BatchCtl* ct
   const uint32_t nunits = ctl->dec_units, n = ctl->ndecomp;
   uint32_t cur = 0xFFFFFFFFu;
   int mode = 2;
-  for (;;) {
-    const uint32_t u = take_ticket(&ctl->tickets[kTicketDecode], &s_u);
-    if (u >= nunits) break;
-    const uint32_t i = find_item(decomps, n, u, [](const BatchDecomp& d) { return d.unit_base; });
+  TicketStream ts{&ctl->tickets[kTicketDecode], &s_u, 0u};
+  for (uint32_t u = ts.first(); u < nunits; u = ts.next()) {
+    const uint32_t i = find_item(ctl->unit_base, n, u);
     const BatchDecomp& d = decomps[i];
     const DecTables* T = d.T;
     if (i != cur) {
@@ -267,11 +317,17 @@ __global__ void batch_finish_kernel(BatchCtl* ctl, const BatchComp* comps,
 
 // ------------------------------------------------------------- per-request state
 // Clear what must start at zero in every request's state: status words,
-// counters, histogram, scan flags (everything before the code table).
+// counters, histogram, scan flags (everything before the code table); and
+// copy each compress request's first histogram unit and tile into the
+// compact arrays the unit search reads.
 __global__ void batch_clear_kernel(BatchCtl* ctl, const BatchComp* comps,
                                    const BatchDecomp* decomps) {
   constexpr uint32_t kWords = (uint32_t)(offsetof(DevState, codes) / 4);
   const uint32_t nc = ctl->ncomp, nd = ctl->ndecomp;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    ctl->hist_base[i] = comps[i].hist_base;
+    ctl->tile_base[i] = comps[i].tile_base;
+  }
   for (uint32_t i = blockIdx.x; i < nc + nd; i += gridDim.x) {
     uint32_t* w = reinterpret_cast<uint32_t*>(i < nc ? comps[i].st : decomps[i - nc].st);
     for (uint32_t k = threadIdx.x; k < kWords; k += blockDim.x) w[k] = 0;
