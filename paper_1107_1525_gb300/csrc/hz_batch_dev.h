@@ -6,7 +6,7 @@
 
 namespace hz {
 
-constexpr uint64_t kBatchHistChunk = 64ull << 10;  // bytes per histogram work unit
+constexpr uint64_t kBatchHistChunk = 256ull << 10;  // bytes per histogram work unit
 
 enum : int { kTicketHist = 0, kTicketSummary = 1, kTicketPack = 2, kTicketDecode = 3, kTickets = 4 };
 

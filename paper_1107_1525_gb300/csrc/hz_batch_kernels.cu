@@ -33,8 +33,15 @@ __device__ __forceinline__ uint32_t find_item(const uint32_t* base, uint32_t cou
 }
 
 // Encoder tiles are handed out in chunks of consecutive tiles, so that a CTA
-// mostly stays inside one request and loads its tables once per chunk.
+// mostly stays inside one request and loads its tables once per chunk: up to
+// kBatchTileChunk tiles, fewer when the batch has too few tiles to give every
+// CTA several chunks.
 constexpr uint32_t kBatchTileChunk = 8;
+
+__device__ __forceinline__ uint32_t tile_chunk(uint32_t ntiles) {
+  const uint32_t k = ntiles / (gridDim.x * 8u);
+  return k < 1 ? 1u : (k > kBatchTileChunk ? kBatchTileChunk : k);
+}
 
 // The request that holds a unit, remembered across calls: a unit inside the
 // last request's range needs no search.  Works for any order of units.
@@ -151,9 +158,10 @@ __global__ void __launch_bounds__(kEncThreads) batch_summary_kernel(BatchCtl* ct
   RequestCursor rc{ctl->tile_base, ncomp, ntiles};
   uint32_t loaded = 0xFFFFFFFFu;  // the request whose lengths are in s_len
   TicketStream ts{&ctl->tickets[kTicketSummary], &s_u, 0u};
-  for (uint32_t u = ts.first(); u * kBatchTileChunk < ntiles; u = ts.next()) {
-    const uint32_t t_end = min(u * kBatchTileChunk + kBatchTileChunk, ntiles);
-    for (uint32_t tile = u * kBatchTileChunk; tile < t_end; ++tile) {
+  const uint32_t K = tile_chunk(ntiles);
+  for (uint32_t u = ts.first(); u * K < ntiles; u = ts.next()) {
+    const uint32_t t_end = min(u * K + K, ntiles);
+    for (uint32_t tile = u * K; tile < t_end; ++tile) {
       const uint32_t i = rc.find(tile);
       const BatchComp& c = comps[i];
       if (c.st->codes.maxlen > (uint32_t)kMaxLen) continue;  // code construction failed
@@ -194,9 +202,10 @@ __global__ void __launch_bounds__(kEncThreads, 3) batch_pack_kernel(BatchCtl* ct
   RequestCursor rc{ctl->tile_base, ncomp, ntiles};
   uint32_t loaded = 0xFFFFFFFFu;  // the request whose tables are in sh
   TicketStream ts{&ctl->tickets[kTicketPack], &s_u, 0u};
-  for (uint32_t u = ts.first(); u * kBatchTileChunk < ntiles; u = ts.next()) {
-    const uint32_t t_end = min(u * kBatchTileChunk + kBatchTileChunk, ntiles);
-    for (uint32_t tile = u * kBatchTileChunk; tile < t_end; ++tile) {
+  const uint32_t K = tile_chunk(ntiles);
+  for (uint32_t u = ts.first(); u * K < ntiles; u = ts.next()) {
+    const uint32_t t_end = min(u * K + K, ntiles);
+    for (uint32_t tile = u * K; tile < t_end; ++tile) {
       const uint32_t i = rc.find(tile);
       const BatchComp& c = comps[i];
       if (!c.st->enc_ok || c.st->error) continue;  // uniform: nothing to pack for this request

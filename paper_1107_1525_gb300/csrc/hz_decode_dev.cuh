@@ -157,14 +157,47 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   __shared__ uint32_t s_l2_total;
   const uint32_t nv = 1u << W, per = (nv + blockDim.x - 1) / blockDim.x;
   uint32_t my_l2 = 0;
+  // single-symbol table first: value v starts the last code (in canonical
+  // order, i.e. by left-justified value) whose W-bit left-justified value is
+  // at most v, if v lies inside its range
+  __shared__ uint32_t s_lj[256];      // left-justified codes of at most W bits, ascending
+  __shared__ uint16_t s_t1[1 << kLutMaxBits];  // symbol | length << 8, 0: no code of <= W bits
+  uint32_t nshort = 0;
+  for (int k = 1; k <= W && k <= (int)maxl; ++k) nshort += cnt[k];
+  if ((uint32_t)t < nshort) {
+    uint32_t k = 1;
+    while (offs[k] + cnt[k] <= (uint32_t)t) ++k;  // the length of sorted code t
+    s_lj[t] = (uint32_t)((first[k] + (t - offs[k])) << (W - k));
+  }
+  __syncthreads();
+  for (uint32_t v = t; v < nv; v += blockDim.x) {
+    uint16_t e1 = 0;
+    if (nshort) {
+      uint32_t lo_i = 0, hi_i = nshort;  // last i with s_lj[i] <= v
+      while (hi_i - lo_i > 1) {
+        const uint32_t mid = (lo_i + hi_i) >> 1;
+        if (s_lj[mid] <= v) lo_i = mid;
+        else hi_i = mid;
+      }
+      if (s_lj[lo_i] <= v) {
+        uint32_t k = 1;
+        while (offs[k] + cnt[k] <= lo_i) ++k;
+        if (v - s_lj[lo_i] < (1u << (W - k))) e1 = (uint16_t)(s_sorted[lo_i] | (k << 8));
+      }
+    }
+    s_t1[v] = e1;
+  }
+  __syncthreads();
   for (uint32_t v = t * per; v < (t + 1) * per && v < nv; ++v) {
-    uint32_t s0 = 0, s1 = 0;
-    const uint32_t l0 = code_at(v, W, s0);
+    const uint32_t e1 = s_t1[v];
+    const uint32_t l0 = e1 >> 8, s0 = e1 & 0xFFu;
     uint32_t e = 0, ext = 0;
     if (l0) {
-      const uint32_t rest = W - l0;
-      const uint32_t l1 = rest ? code_at(v & ((1u << rest) - 1u), (int)rest, s1) : 0u;
-      e = l1 ? lut_entry(s0, s1, 2, l0 + l1, l0) : lut_entry(s0, 0, 1, l0, l0);
+      // the next code, when it fits in the W - l0 bits that follow
+      const uint32_t e2 = l0 < (uint32_t)W ? s_t1[(v << l0) & (nv - 1)] : 0u;
+      const uint32_t l1 = e2 >> 8;
+      e = (l1 && l1 <= (uint32_t)W - l0) ? lut_entry(s0, e2 & 0xFFu, 2, l0 + l1, l0)
+                                          : lut_entry(s0, 0, 1, l0, l0);
     } else {
       // the longest code (of up to 32 bits) that starts with v
       for (uint32_t k = (uint32_t)W + 1; k <= maxl && k <= 32; ++k) {
