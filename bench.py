@@ -46,9 +46,12 @@ WORKLOADS = {
                          desc="2^28 int8 residuals of a smooth 512x512x1024 Gaussian field, "
                               "16 KiB blocks"),
 }
-# DRAM traffic per launch from an ncu capture of the same kernel revision
-# (dram__bytes_read.sum + dram__bytes_write.sum); None until captured.
-NCU_TRAFFIC = {}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# ncu captures of the current kernel revisions on the 256 MiB profiling case,
+# scaled by the units processed to a 1 GiB launch (profiles/*.md); other
+# workloads report null.
+NCU_TRAFFIC = {"mixed-1GiB": {"decode": 4 * (448_804_096 + 241_734_144),
+                              "encode_pack": 4 * (272_070_912 + 165_756_928)}}
 
 
 def load_peaks():
@@ -555,7 +558,7 @@ def run_gpu(args, world, rank, local, pg):
         cpu = {"value": xs.size / (te + td) / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"{xs.size // MiB} MiB host sample of the workload (equal slices of each "
                          f"segment kind), one compress + decompress, single thread"}
-    traffic = NCU_TRAFFIC.get(dom)
+    traffic = NCU_TRAFFIC.get(args.workload, {}).get(dom)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
