@@ -19,6 +19,11 @@ struct ProfRec {
   cudaEvent_t a, b;
 };
 
+// Host-buffer decompression of large streams with an index runs as a
+// pipeline of this many block groups (copy in, decode, copy out overlap).
+constexpr int kPipeGroups = 4;
+constexpr uint64_t kPipeMinBytes = 32ull << 20;
+
 struct hz_ctx {
   int device = 0;
   int num_sms = 0;
@@ -38,6 +43,9 @@ struct hz_ctx {
   uint64_t d_hout_cap = 0;
   uint64_t* d_len = nullptr;
   uint64_t* h_len = nullptr;
+  // pipelined host-buffer decode: copy-in and copy-out streams, group events
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t e_start = nullptr, e_in[kPipeGroups] = {}, e_dec[kPipeGroups] = {};
   // options
   int opt_index = 1;
   int opt_profile = 0;
@@ -156,6 +164,13 @@ hz_status hz_create(hz_ctx** out, int device, uint64_t mem_budget_bytes) {
     return HZ_ERR_NOMEM;
   }
   c->batch = hz_batch_create(c->device, c->num_sms, mem_budget_bytes);
+  cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&c->e_start, cudaEventDisableTiming);
+  for (int g = 0; g < kPipeGroups; ++g) {
+    cudaEventCreateWithFlags(&c->e_in[g], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->e_dec[g], cudaEventDisableTiming);
+  }
   hz_tune_load_cache(c);
   *out = c;
   return HZ_OK;
@@ -166,6 +181,15 @@ void hz_destroy(hz_ctx* c) {
   DeviceGuard g(c->device);
   cudaDeviceSynchronize();
   if (c->batch) hz_batch_destroy(c->batch);
+  if (c->s_in) cudaStreamSynchronize(c->s_in);
+  if (c->s_out) cudaStreamSynchronize(c->s_out);
+  if (c->e_start) cudaEventDestroy(c->e_start);
+  for (int g = 0; g < kPipeGroups; ++g) {
+    if (c->e_in[g]) cudaEventDestroy(c->e_in[g]);
+    if (c->e_dec[g]) cudaEventDestroy(c->e_dec[g]);
+  }
+  if (c->s_in) cudaStreamDestroy(c->s_in);
+  if (c->s_out) cudaStreamDestroy(c->s_out);
   for (auto& r : c->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -426,6 +450,8 @@ hz_status hz_decompress(hz_ctx* c, const uint8_t* d_in, uint64_t in_len, uint8_t
   a.chase_index = c->d_chase;
   a.chase_cap = c->chase_cap;
   a.lut_bits = c->opt_lut_bits;
+  a.k_begin = 0;
+  a.k_end = 0xFFFFFFFFu;
   hz_status st = launch(c, K_DECODE_SETUP, s, [&] { return launch_decode_setup(a, c->d_dec, s); });
   if (st != HZ_OK) return st;
   st = launch(c, K_DECODE, s, [&] {
@@ -434,6 +460,104 @@ hz_status hz_decompress(hz_ctx* c, const uint8_t* d_in, uint64_t in_len, uint8_t
   if (st != HZ_OK) return st;
   return launch(c, K_DECODE_GENERIC, s,
                 [&] { return launch_decode_generic(a, c->d_dec, c->num_sms, s); });
+}
+
+// Decompress a large host-resident stream with an index as a pipeline of
+// kPipeGroups groups of consecutive blocks: each group's records are copied
+// in on one stream, decoded as soon as they have landed (the decoder needs
+// only the header, the index and a block's own record), and its output is
+// copied out on a third stream while later groups are still coming in.  The
+// host reads the header and the index from the caller's buffer only to cut
+// the groups.  Returns HZ_PENDING, having done nothing, when the stream is
+// small, has no index, has blocks too large for the fast decoder, or its
+// header or index does not describe the buffer (the plain path then reports
+// what is wrong).  On a decoding error the output buffer may hold partial
+// data; the status says so.
+static hz_status decompress_host_pipelined(hz_ctx* c, const uint8_t* h_in, uint64_t in_len,
+                                           uint8_t* h_out, uint64_t out_cap, uint64_t* out_len,
+                                           cudaStream_t s) {
+  if (in_len < kPipeMinBytes || !c->s_in) return HZ_PENDING;
+  uint32_t flags, B, nb;
+  uint64_t n;
+  memcpy(&flags, h_in + 4, 4);
+  memcpy(&n, h_in + 8, 8);
+  memcpy(&B, h_in + 16, 4);
+  memcpy(&nb, h_in + 20, 4);
+  if (memcmp(h_in, "HZB1", 4) != 0 || !(flags & kFlagIndex) || B == 0 || B > 65536 ||
+      nb < (uint32_t)kPipeGroups || (uint64_t)nb != (n + B - 1) / B || n > out_cap)
+    return HZ_PENDING;
+  const uint64_t blocks_at = kHeaderBytes + 4ull * nb;
+  if (blocks_at > in_len) return HZ_PENDING;
+  // group g covers blocks [kg[g], kg[g + 1]) and stream bytes [at[g], at[g + 1])
+  uint32_t kg[kPipeGroups + 1];
+  uint64_t at[kPipeGroups + 1];
+  for (int gi = 0; gi <= kPipeGroups; ++gi) {
+    kg[gi] = (uint32_t)((uint64_t)nb * gi / kPipeGroups);
+    uint32_t O = 0;
+    if (kg[gi] < nb) memcpy(&O, h_in + kHeaderBytes + 4ull * kg[gi], 4);
+    at[gi] = kg[gi] < nb ? blocks_at + 4ull * O : in_len;
+    if (at[gi] > in_len || (gi && at[gi] < at[gi - 1])) return HZ_PENDING;
+  }
+  at[0] = 0;  // the first group also brings the header and the index
+  DecodeArgs a;
+  a.in = c->d_hin;
+  a.in_len = in_len;
+  a.out = c->d_hout;
+  a.out_cap = out_cap;
+  a.out_len = c->d_len;
+  a.st = c->d_state;
+  a.chase_index = c->d_chase;
+  a.chase_cap = c->chase_cap;
+  a.lut_bits = c->opt_lut_bits;
+  // the caller's stream may have work on these buffers queued: start after it
+  if (cudaEventRecord(c->e_start, s) != cudaSuccess ||
+      cudaStreamWaitEvent(c->s_in, c->e_start, 0) != cudaSuccess ||
+      cudaStreamWaitEvent(c->s_out, c->e_start, 0) != cudaSuccess)
+    return HZ_ERR_CUDA;
+  for (int gi = 0; gi < kPipeGroups; ++gi) {
+    if (cudaMemcpyAsync(c->d_hin + at[gi], h_in + at[gi], at[gi + 1] - at[gi],
+                        cudaMemcpyHostToDevice, c->s_in) != cudaSuccess ||
+        cudaEventRecord(c->e_in[gi], c->s_in) != cudaSuccess)
+      return HZ_ERR_CUDA;
+  }
+  hz_status st = HZ_OK;
+  for (int gi = 0; gi < kPipeGroups && st == HZ_OK; ++gi) {
+    if (cudaStreamWaitEvent(s, c->e_in[gi], 0) != cudaSuccess) st = HZ_ERR_CUDA;
+    if (st == HZ_OK && gi == 0)
+      st = launch(c, K_DECODE_SETUP, s, [&] { return launch_decode_setup(a, c->d_dec, s); });
+    a.k_begin = kg[gi];
+    a.k_end = kg[gi + 1];
+    if (st == HZ_OK)
+      st = launch(c, K_DECODE, s, [&] {
+        return launch_decode_blocks(a, c->d_dec, c->opt_dec_threads, c->num_sms, s);
+      });
+    if (st == HZ_OK && cudaEventRecord(c->e_dec[gi], s) != cudaSuccess) st = HZ_ERR_CUDA;
+    if (st == HZ_OK && cudaStreamWaitEvent(c->s_out, c->e_dec[gi], 0) != cudaSuccess)
+      st = HZ_ERR_CUDA;
+    const uint64_t o0 = (uint64_t)kg[gi] * B;
+    const uint64_t o1 = gi + 1 < kPipeGroups ? (uint64_t)kg[gi + 1] * B : n;
+    if (st == HZ_OK && o1 > o0 &&
+        cudaMemcpyAsync(h_out + o0, c->d_hout + o0, o1 - o0, cudaMemcpyDeviceToHost, c->s_out) !=
+            cudaSuccess)
+      st = HZ_ERR_CUDA;
+  }
+  a.k_begin = 0;
+  a.k_end = 0xFFFFFFFFu;
+  if (st == HZ_OK)
+    st = launch(c, K_DECODE_GENERIC, s,
+                [&] { return launch_decode_generic(a, c->d_dec, c->num_sms, s); });
+  const bool in_done = cudaStreamSynchronize(c->s_in) == cudaSuccess;
+  const bool out_done = cudaStreamSynchronize(c->s_out) == cudaSuccess;
+  if (st != HZ_OK) {
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  if (cudaMemcpyAsync(c->h_len, c->d_len, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return HZ_ERR_CUDA;
+  st = hz_sync(c, s);
+  if (st == HZ_OK && (!in_done || !out_done)) st = HZ_ERR_CUDA;
+  *out_len = *c->h_len;
+  return st;
 }
 
 hz_status hz_compress_host(hz_ctx* c, const uint8_t* h_in, uint64_t n, uint32_t block_size,
@@ -469,6 +593,8 @@ hz_status hz_decompress_host(hz_ctx* c, const uint8_t* h_in, uint64_t in_len, ui
   hz_status st = grow((void**)&c->d_hin, &c->d_hin_cap, in_len ? in_len : 16);
   if (st == HZ_OK) st = grow((void**)&c->d_hout, &c->d_hout_cap, out_cap ? out_cap : 16);
   if (st != HZ_OK) return st;
+  st = decompress_host_pipelined(c, h_in, in_len, h_out, out_cap, out_len, s);
+  if (st != HZ_PENDING) return st;  // HZ_PENDING: the stream does not suit the pipeline
   if (cudaMemcpyAsync(c->d_hin, h_in, in_len, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return HZ_ERR_CUDA;
   st = hz_decompress(c, c->d_hin, in_len, c->d_hout, out_cap, c->d_len, stream);

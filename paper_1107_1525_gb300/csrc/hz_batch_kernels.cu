@@ -87,6 +87,8 @@ __device__ __forceinline__ DecodeArgs decomp_args(const BatchDecomp& d) {
   a.chase_index = nullptr;  // batched streams must carry the block-offset index
   a.chase_cap = 0;
   a.lut_bits = (int)d.lut_bits;
+  a.k_begin = 0;
+  a.k_end = 0xFFFFFFFFu;
   return a;
 }
 

@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(kFastThreads) decode_fast_kernel(DecodeArgs a,
   const uint32_t warps = kFastThreads / 32;
   const uint32_t stride = gridDim.x * warps;
   const int mode = fast_mode(T, sh.c);
-  for (uint32_t k = blockIdx.x * warps + (threadIdx.x >> 5); k < sh.c.nb; k += stride)
+  const uint32_t k_end = a.k_end < sh.c.nb ? a.k_end : sh.c.nb;
+  for (uint32_t k = a.k_begin + blockIdx.x * warps + (threadIdx.x >> 5); k < k_end; k += stride)
     decode_block_fast(a, sh, k, mode);
 }
 
@@ -79,7 +80,15 @@ cudaError_t launch_decode_blocks(const DecodeArgs& a, const DecTables* T, int th
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_fast_kernel, kFastThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  decode_fast_kernel<<<num_sms * per_sm, kFastThreads, 0, s>>>(a, T);
+  uint64_t grid = (uint64_t)num_sms * per_sm;
+  // a block range shorter than the resident warps needs fewer CTAs (the
+  // block count itself is only known on the device: an unbounded range keeps
+  // the full grid)
+  if (a.k_end != 0xFFFFFFFFu) {
+    const uint64_t need = ((uint64_t)(a.k_end - a.k_begin) + kFastThreads / 32 - 1) / (kFastThreads / 32);
+    if (need < grid) grid = need ? need : 1;
+  }
+  decode_fast_kernel<<<(unsigned)grid, kFastThreads, 0, s>>>(a, T);
   return cudaGetLastError();
 }
 

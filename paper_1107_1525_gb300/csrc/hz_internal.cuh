@@ -153,6 +153,7 @@ struct DecodeArgs {
   uint32_t* chase_index;    // scratch index for streams without one (nb words)
   uint32_t chase_cap;       // capacity of chase_index in entries
   int lut_bits;
+  uint32_t k_begin, k_end;  // blocks the fast kernel decodes: [k_begin, min(k_end, nb))
 };
 
 // Each returns the cudaError_t of its launch.
