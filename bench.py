@@ -430,6 +430,103 @@ def _slice(tr, item):
     return tr["arenas"][off:off + int(item["src_len"])]
 
 
+# ------------------------------------------------------------------ experiments
+def _record_bits(s):
+    """Per-block payload bits of a device stream with an index (delimiters)."""
+    import torch
+    nb = int(np.frombuffer(s[20:24].cpu().numpy().tobytes(), dtype="<u4")[0])
+    idx = s[280:280 + 4 * nb].view(torch.int32).long()
+    words = s[280 + 4 * nb:].view(torch.int32)
+    return words[idx].long() & 0xFFFFFFFF, nb
+
+
+def _time_ms(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_experiments(args):
+    """The block-size question of the paper's Fig. 5 (format overhead and speed against
+    block size) and the cost of decoding the paper's original layout, without the
+    stored offset index.  Prints one JSON line."""
+    import torch
+
+    import datagen
+    import paper_1107_1525_gb300.hz as hz
+    from paper_1107_1525_gb300 import build
+    build.build()
+    dev = torch.device("cuda:0")
+    ctx = hz.Context(0)
+    inputs = {
+        "zipf-1MiB": datagen.zipf_buffer(MiB, s=1.1, seed=0, device=dev),
+        "mixed-256MiB": datagen.mixed_buffer(n=256 * MiB, segment=64 * MiB, seed=2, device=dev),
+        "field-256MiB": datagen.gaussian_field_residuals(shape=(512, 512, 1024), seed=1,
+                                                         device=dev),
+    }
+    sweep = []
+    for name, x in inputs.items():
+        n = x.numel()
+        y = torch.empty_like(x)
+        ol = torch.zeros(1, dtype=torch.int64, device=dev)
+        for B in (256, 1024, 4096, 16384, 65536, 262144, 1048576):
+            if B > n:
+                continue
+            cap = hz.hz_compress_bound(n, B)
+            out = torch.empty(cap, dtype=torch.uint8, device=dev)
+            hz.hz_compress(ctx, x, n, B, None, out, cap, ol)
+            if hz.hz_sync(ctx):
+                raise RuntimeError(f"compress {name} B={B}")
+            size = int(ol.item())
+            s = out[:size]
+            bits, nb = _record_bits(s)
+            payload = int(bits.sum())
+            # per block: 32-bit delimiter + zero padding to a word (Sec. 2.1)
+            blk = 32 * nb + int(((32 - (bits % 32)) % 32).sum())
+            reps = 20 if n <= 16 * MiB else 5
+            c_ms = _time_ms(lambda: hz.hz_compress(ctx, x, n, B, None, out, cap, ol), reps)
+            d_ms = _time_ms(lambda: hz.hz_decompress(ctx, s, size, y, n, ol), reps)
+            if hz.hz_sync(ctx) or not torch.equal(x, y):
+                raise RuntimeError(f"round trip {name} B={B}")
+            sweep.append({"input": name, "block_size": B, "blocks": nb, "stream_bytes": size,
+                          "payload_bits": payload,
+                          "block_overhead_bits_per_block": blk / nb,
+                          "block_overhead_pct": 100.0 * blk / payload,
+                          "container_overhead_pct": 100.0 * (8 * size - payload) / payload,
+                          "compress_gbs": n / c_ms / 1e6, "decompress_gbs": n / d_ms / 1e6})
+    # the paper's layout: no stored index, the decoder chases the delimiters
+    x = datagen.mixed_buffer(n=GiB, segment=64 * MiB, seed=2, device=dev)
+    y = torch.empty_like(x)
+    ol = torch.zeros(1, dtype=torch.int64, device=dev)
+    cost = {}
+    for index in (1, 0):
+        ctx.set_option(hz.HZ_OPT_INDEX, index)
+        s = hz.compress(x, 65536, ctx=ctx)
+        ctx.set_option(hz.HZ_OPT_INDEX, 1)
+        d_ms = _time_ms(lambda: hz.hz_decompress(ctx, s, s.numel(), y, x.numel(), ol), 5)
+        ctx.profile_read()
+        ctx.set_option(hz.HZ_OPT_PROFILE, 1)
+        hz.hz_decompress(ctx, s, s.numel(), y, x.numel(), ol)
+        prof = dict((k, v) for k, v in ctx.profile_read())
+        ctx.set_option(hz.HZ_OPT_PROFILE, 0)
+        if hz.hz_sync(ctx) or not torch.equal(x, y):
+            raise RuntimeError("index cost round trip")
+        cost["with_index" if index else "without_index"] = {
+            "stream_bytes": s.numel(), "decompress_ms": d_ms,
+            "decode_setup_ms": prof.get("decode_setup"), "decode_ms": prof.get("decode")}
+    cost["workload"] = "1 GiB mix, 64 KiB blocks (16384 records)"
+    ctx.close()
+    print(json.dumps({"experiments": {"block_size_sweep": sweep, "index_cost": cost}}),
+          flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, world, rank, local, pg):
     import torch
@@ -599,6 +696,8 @@ def main():
     ap.add_argument("--cpu-sample-mib", type=int, default=192,
                     help="host sample for the cpu_baseline key of the GPU arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--experiments", action="store_true",
+                    help="block-size sweep and index cost instead of the bench line")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-buffer batch")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-reps", type=int, default=6)
@@ -610,7 +709,10 @@ def main():
     args = ap.parse_args()
     world, rank, local, pg = dist_setup(args)
     try:
-        if args.impl == "reference":
+        if args.experiments:
+            if rank == 0:
+                run_experiments(args)
+        elif args.impl == "reference":
             run_reference(args, world, rank, pg)
         else:
             run_gpu(args, world, rank, local, pg)
