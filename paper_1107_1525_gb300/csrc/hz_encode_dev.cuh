@@ -370,10 +370,38 @@ static __device__ __forceinline__ void copy_out(const uint32_t* stage, uint32_t*
   }
 }
 
+// pack_entries for codes of up to 32 bits: the symbols in x[], their code
+// lengths six bits each, five to a word, in lp[]; the codes are looked up.
+__device__ __forceinline__ void pack_entries_wide(const PackShared& sh,
+                                                  const uint32_t (&x)[kEncSymPerThread / 4],
+                                                  const uint32_t (&lp)[(kEncSymPerThread + 4) / 5],
+                                                  uint32_t* st, uint32_t wrel, uint32_t nacc) {
+  bool first_shared = nacc != 0;
+  uint64_t acc = 0;  // fewer than 32 pending bits before each code of at most 32
+#pragma unroll
+  for (int i = 0; i < kEncSymPerThread; ++i) {
+    const uint32_t l = (lp[i / 5] >> (6 * (i % 5))) & 63u;
+    const uint32_t c = l ? sh.code_lo[sym_of(x, i)] : 0u;  // l = 0 past the thread's symbols
+    acc = (acc << l) | c;
+    nacc += l;
+    if (nacc >= 32) {
+      nacc -= 32;
+      const uint32_t v = (uint32_t)(acc >> nacc);
+      if (first_shared) atomicOr(st + wrel, v);
+      else st[wrel] = v;
+      first_shared = false;
+      ++wrel;
+    }
+  }
+  if (nacc) atomicOr(st + wrel, (uint32_t)(acc << (32 - nacc)));
+}
+
 // Single-record path: the tile lies inside one record (which may start at its
-// first symbol) and codes have at most 26 bits; thread positions come from a
-// plain scan of bit counts.
-template <bool kPair>
+// first symbol); thread positions come from a plain scan of bit counts.
+// kKind 0: codes of at most 16 bits, packed two at a time; 1: at most 26
+// bits (code and length in one cached word); 2: at most 32 bits (lengths
+// cached, codes looked up again while packing).
+template <int kKind>
 __device__ __noinline__ void pack_tile_single(PackShared& sh, uint32_t tile, const TileGeom g,
                                                  uint32_t* rec_words) {
   const EncodeArgs& a = sh.a;
@@ -385,11 +413,18 @@ __device__ __noinline__ void pack_tile_single(PackShared& sh, uint32_t tile, con
   uint32_t x[kEncSymPerThread / 4];
   load_symbols(a.in + g.g0, g.my_cnt, x);
   uint32_t e[kEncSymPerThread];
+  uint32_t lp[(kEncSymPerThread + 4) / 5] = {};
   uint32_t bits = 0;
 #pragma unroll
   for (int i = 0; i < kEncSymPerThread; ++i) {
-    e[i] = i < g.my_cnt ? sh.entry[sym_of(x, i)] : 0u;
-    bits += e[i] & 63u;
+    if (kKind == 2) {  // codes are looked up again while packing
+      const uint32_t l = i < g.my_cnt ? sh.len[sym_of(x, i)] : 0u;
+      lp[i / 5] |= l << (6 * (i % 5));
+      bits += l;
+    } else {
+      e[i] = i < g.my_cnt ? sh.entry[sym_of(x, i)] : 0u;
+      bits += e[i] & 63u;
+    }
   }
   uint32_t inc = bits;
 #pragma unroll
@@ -423,7 +458,8 @@ __device__ __noinline__ void pack_tile_single(PackShared& sh, uint32_t tile, con
   __syncthreads();
   if (bits) {
     const uint32_t p = b0 + ex;
-    pack_entries<kPair>(e, sh.stage + off, (p >> 5) - (b0 >> 5), p & 31u);
+    if (kKind == 2) pack_entries_wide(sh, x, lp, sh.stage + off, (p >> 5) - (b0 >> 5), p & 31u);
+    else pack_entries<kKind == 0>(e, sh.stage + off, (p >> 5) - (b0 >> 5), p & 31u);
   }
   __syncthreads();
   // the last word belongs to the next tile when the record goes on mid-word
@@ -662,31 +698,6 @@ __device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, co
   }
 }
 
-// Tile loops, one per path, each compiled on its own so that the common
-// paths keep their registers.
-template <int kMode>  // 0: single-record/chunked with pairs, 1: same with single codes
-__device__ __forceinline__ void pack_tiles_fast(const EncodeArgs& a, PackShared& sh,
-                                             uint32_t* rec_words) {
-  const bool chunked_ok = a.fdB.d % kEncSymPerThread == 0;
-  for (uint32_t i = blockIdx.x; i < a.ntiles; i += gridDim.x) {
-    const uint32_t tile = a.ntiles - 1 - i;  // last tiles first: their input is still in L2
-    const TileGeom g = tile_geom(tile, (uint32_t)a.n, a.fdB);
-    if (!g.interior_start) pack_tile_single<kMode == 0>(sh, tile, g, rec_words);
-    else if (chunked_ok) pack_tile_chunked<kMode == 0>(sh, tile, g, rec_words);
-    else pack_tile_general<false>(sh, tile, g, rec_words);
-    __syncthreads();
-  }
-}
-
-static __device__ __forceinline__ void pack_tiles_long(const EncodeArgs& a, PackShared& sh,
-                                             uint32_t* rec_words) {
-  for (uint32_t i = blockIdx.x; i < a.ntiles; i += gridDim.x) {
-    const uint32_t tile = a.ntiles - 1 - i;
-    pack_tile_general<true>(sh, tile, tile_geom(tile, (uint32_t)a.n, a.fdB), rec_words);
-    __syncthreads();
-  }
-}
-
 // Load the code table of the buffer `a` describes into the packing tables.
 static __device__ __forceinline__ void pack_load_tables(PackShared& sh, const EncodeArgs& a) {
   const CodeTable* ct = &a.st->codes;
@@ -708,9 +719,11 @@ static __device__ __forceinline__ void pack_one_tile(PackShared& sh, uint32_t ti
       a.out + kHeaderBytes + ((a.flags & kFlagIndex) ? 4ull * a.nb : 0ull));
   const TileGeom g = tile_geom(tile, (uint32_t)a.n, a.fdB);
   const bool chunked_ok = a.fdB.d % kEncSymPerThread == 0;
-  if (maxlen > 26) pack_tile_general<true>(sh, tile, g, rec_words);
-  else if (!g.interior_start && maxlen <= 16) pack_tile_single<true>(sh, tile, g, rec_words);
-  else if (!g.interior_start) pack_tile_single<false>(sh, tile, g, rec_words);
+  if (maxlen > 32) pack_tile_general<true>(sh, tile, g, rec_words);
+  else if (!g.interior_start && maxlen <= 16) pack_tile_single<0>(sh, tile, g, rec_words);
+  else if (!g.interior_start && maxlen <= 26) pack_tile_single<1>(sh, tile, g, rec_words);
+  else if (!g.interior_start) pack_tile_single<2>(sh, tile, g, rec_words);
+  else if (maxlen > 26) pack_tile_general<true>(sh, tile, g, rec_words);
   else if (chunked_ok && maxlen <= 16) pack_tile_chunked<true>(sh, tile, g, rec_words);
   else if (chunked_ok) pack_tile_chunked<false>(sh, tile, g, rec_words);
   else pack_tile_general<false>(sh, tile, g, rec_words);
