@@ -10,11 +10,12 @@ namespace hz {
 static __device__ void build_codes_device(DevState* st, int from_hist, const LenParam& given,
                                    uint64_t n, uint32_t B, uint32_t nb, uint32_t flags,
                                    uint8_t* out, uint64_t out_cap, uint64_t* out_len) {
-  __shared__ uint64_t s_freq[256];
-  __shared__ uint64_t leaf_w[256];
+  // weights fit 32 bits: every count and every sum of counts is at most n < 2^32
+  __shared__ uint32_t s_freq[256];
+  __shared__ uint32_t leaf_w[256];
   __shared__ int leaf_sym[256];
   __shared__ int leaf_par[256];
-  __shared__ uint64_t int_w[256];
+  __shared__ uint32_t int_w[256];
   __shared__ int anc[2][256];
   __shared__ int dep[2][256];
   __shared__ uint32_t s_len[256];
@@ -27,13 +28,13 @@ static __device__ void build_codes_device(DevState* st, int from_hist, const Len
     s_freq[t] = st->hist[t];
     s_len[t] = 0;
     __syncthreads();
-    const uint64_t f = s_freq[t];
+    const uint32_t f = s_freq[t];
     const int present = f > 0;
     const int m = __syncthreads_count(present);
     if (present) {
       int r = 0;
       for (int u = 0; u < 256; ++u) {
-        uint64_t g = s_freq[u];
+        const uint32_t g = s_freq[u];
         r += (g > 0) & ((g < f) | ((g == f) & (u < t)));
       }
       leaf_w[r] = f;
@@ -46,7 +47,7 @@ static __device__ void build_codes_device(DevState* st, int from_hist, const Len
       if (t == 0) {
         int li = 0, qh = 0, qt = 0;
         for (int k = 0; k < m - 1; ++k) {
-          uint64_t w = 0;
+          uint32_t w = 0;
 #pragma unroll
           for (int r = 0; r < 2; ++r) {
             bool take_leaf = li < m && (qh >= qt || leaf_w[li] <= int_w[qh]);

@@ -37,8 +37,17 @@ __global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs 
   for (int s = threadIdx.x; s < 256; s += kEncThreads) s_len[s] = ct->len[s];
   __syncthreads();
   bool bad = false;
-  for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
-    summary_tile(a, tile, s_len, s_wsum, s_warp, bad);
+  // the next tile's symbols are loaded while the current one is summarised
+  uint32_t x[kEncSymPerThread / 4], xn[kEncSymPerThread / 4];
+  uint32_t tile = blockIdx.x;
+  if (tile < a.ntiles) load_tile_symbols(a, tile, x);
+  for (; tile < a.ntiles; tile += gridDim.x) {
+    const uint32_t nt = tile + gridDim.x;
+    if (nt < a.ntiles) load_tile_symbols(a, nt, xn);
+    summary_tile_x(a, tile, x, s_len, s_wsum, s_warp, bad);
+#pragma unroll
+    for (int k = 0; k < kEncSymPerThread / 4; ++k) x[k] = xn[k];
+  }
   if (bad) set_error(a.st, HZ_ERR_ARG, 0x200);  // a byte without a code (caller's code table)
 }
 

@@ -147,13 +147,20 @@ __device__ __forceinline__ Summary thread_summary(const uint32_t (&x)[kEncSymPer
 // =================================================================== pass 1
 // Summary of one tile into a.tiles[tile].  s_len: the code lengths (shared),
 // s_wsum / s_warp: per-warp scratch (shared).  Ends with a CTA barrier.
-static __device__ __forceinline__ void summary_tile(const EncodeArgs& a, uint32_t tile,
-                                             const uint8_t* s_len, uint32_t* s_wsum,
-                                             Summary* s_warp, bool& bad) {
+// The thread's symbols of `tile` (see load_symbols).
+static __device__ __forceinline__ void load_tile_symbols(const EncodeArgs& a, uint32_t tile,
+                                                         uint32_t (&x)[kEncSymPerThread / 4]) {
+  const TileGeom g = tile_geom(tile, (uint32_t)a.n, a.fdB);
+  load_symbols(a.in + g.g0, g.my_cnt, x);
+}
+
+// summary_tile with the thread's symbols already loaded.
+static __device__ __forceinline__ void summary_tile_x(const EncodeArgs& a, uint32_t tile,
+                                                      const uint32_t (&x)[kEncSymPerThread / 4],
+                                                      const uint8_t* s_len, uint32_t* s_wsum,
+                                                      Summary* s_warp, bool& bad) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const TileGeom g = tile_geom(tile, (uint32_t)a.n, a.fdB);
-  uint32_t x[kEncSymPerThread / 4];
-  load_symbols(a.in + g.g0, g.my_cnt, x);
   if (!g.interior_start) {
     // the tile lies inside one record (which may start at its first symbol)
     uint32_t bits = 0, minl = 64;
@@ -202,6 +209,14 @@ static __device__ __forceinline__ void summary_tile(const EncodeArgs& a, uint32_
     }
   }
   __syncthreads();
+}
+
+static __device__ __forceinline__ void summary_tile(const EncodeArgs& a, uint32_t tile,
+                                             const uint8_t* s_len, uint32_t* s_wsum,
+                                             Summary* s_warp, bool& bad) {
+  uint32_t x[kEncSymPerThread / 4];
+  load_tile_symbols(a, tile, x);
+  summary_tile_x(a, tile, x, s_len, s_wsum, s_warp, bad);
 }
 
 // The stream size, from the state after the last tile, and the capacity check.
