@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "hz_batch.h"
+#include "hz_chase.h"
 #include "hz_internal.cuh"
 
 using namespace hz;
@@ -23,6 +24,8 @@ struct ProfRec {
 // pipeline of this many block groups (copy in, decode, copy out overlap).
 constexpr int kPipeGroups = 4;
 constexpr uint64_t kPipeMinBytes = 32ull << 20;
+// Streams without an index at least this long get the parallel chase.
+constexpr uint64_t kChaseParallelMin = 8ull << 20;
 
 struct hz_ctx {
   int device = 0;
@@ -43,6 +46,14 @@ struct hz_ctx {
   uint64_t d_hout_cap = 0;
   uint64_t* d_len = nullptr;
   uint64_t* h_len = nullptr;
+  // streams without an index: the setup kernel sets *h_seen (mapped pinned
+  // memory) when it meets one; from then on large streams get the parallel
+  // chase and its scratch
+  uint32_t* h_seen = nullptr;
+  uint32_t* d_seen = nullptr;
+  uint8_t* d_chase_work = nullptr;
+  uint64_t chase_work_cap = 0;
+  hz::ChaseScratch cs{};
   // pipelined host-buffer decode: copy-in and copy-out streams, group events
   cudaStream_t s_in = nullptr, s_out = nullptr;
   cudaEvent_t e_start = nullptr, e_in[kPipeGroups] = {}, e_dec[kPipeGroups] = {};
@@ -164,6 +175,16 @@ hz_status hz_create(hz_ctx** out, int device, uint64_t mem_budget_bytes) {
     return HZ_ERR_NOMEM;
   }
   c->batch = hz_batch_create(c->device, c->num_sms, mem_budget_bytes);
+  if (cudaHostAlloc(&c->h_seen, sizeof(uint32_t), cudaHostAllocMapped) == cudaSuccess) {
+    *c->h_seen = 0;
+    if (cudaHostGetDevicePointer((void**)&c->d_seen, c->h_seen, 0) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_seen = nullptr;
+    }
+  } else {
+    cudaGetLastError();
+    c->h_seen = nullptr;
+  }
   cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking);
   cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking);
   cudaEventCreateWithFlags(&c->e_start, cudaEventDisableTiming);
@@ -189,6 +210,8 @@ void hz_destroy(hz_ctx* c) {
     if (c->e_dec[g]) cudaEventDestroy(c->e_dec[g]);
   }
   if (c->s_in) cudaStreamDestroy(c->s_in);
+  cudaFree(c->d_chase_work);
+  if (c->h_seen) cudaFreeHost(c->h_seen);
   if (c->s_out) cudaStreamDestroy(c->s_out);
   for (auto& r : c->prof) {
     cudaEventDestroy(r.a);
@@ -274,7 +297,7 @@ uint32_t hz_tuned_block_size(hz_ctx* c, uint64_t n) {
 const char* hz_kernel_name(int32_t id) {
   static const char* names[] = {"histogram",   "build_codes",  "encode_summary", "encode_scan",
                                 "encode_pack", "decode_setup", "decode",         "decode_generic",
-                                "batch"};
+                                "batch",       "decode_chase"};
   if (id < 0 || id >= (int32_t)(sizeof(names) / sizeof(names[0]))) return "?";
   return names[id];
 }
@@ -433,6 +456,47 @@ hz_status hz_compress(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32_t block
   return st;
 }
 
+// Scratch of the parallel chase for a stream of in_len bytes (one allocation
+// carved into the ChaseScratch arrays).
+static hz_status ensure_chase_scratch(hz_ctx* c, uint64_t in_len) {
+  const uint64_t bm = (in_len / 4 + 31) / 32 + 2;
+  if (bm > 0xFFFFFFF0ull) return HZ_ERR_ARG;
+  const uint64_t ccap = (uint64_t)c->chase_cap + 65536, cta = 4096;
+  const uint64_t words = 4 + cta + 2 * bm + 5 * ccap + c->chase_cap;
+  if (words * 4 > c->chase_work_cap) {
+    cudaFree(c->d_chase_work);
+    c->d_chase_work = nullptr;
+    c->chase_work_cap = 0;
+    if (cudaMalloc(&c->d_chase_work, words * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return HZ_ERR_NOMEM;
+    }
+    c->chase_work_cap = words * 4;
+  }
+  uint32_t* p = reinterpret_cast<uint32_t*>(c->d_chase_work);
+  hz::ChaseScratch& cs = c->cs;
+  cs.bar = p;
+  cs.flag = p + 2;
+  p += 4;
+  cs.cta_tot = p;
+  cs.cta_cap = (uint32_t)cta;
+  p += cta;
+  cs.bitmap = p;
+  p += bm;
+  cs.base = p;
+  p += bm;
+  cs.bm_cap = (uint32_t)bm;
+  cs.pos = p;
+  cs.s0 = p + ccap;
+  cs.s1 = p + 2 * ccap;
+  cs.r0 = p + 3 * ccap;
+  cs.r1 = p + 4 * ccap;
+  cs.c_cap = (uint32_t)ccap;
+  p += 5 * ccap;
+  cs.hits = p;
+  return HZ_OK;
+}
+
 hz_status hz_decompress(hz_ctx* c, const uint8_t* d_in, uint64_t in_len, uint8_t* d_out,
                         uint64_t out_cap, uint64_t* d_out_len, void* stream) {
   if (!c || !d_in || !d_out_len || ((uintptr_t)d_in & 3) || ((uintptr_t)d_out_len & 7))
@@ -452,8 +516,18 @@ hz_status hz_decompress(hz_ctx* c, const uint8_t* d_in, uint64_t in_len, uint8_t
   a.lut_bits = c->opt_lut_bits;
   a.k_begin = 0;
   a.k_end = 0xFFFFFFFFu;
+  a.seen_no_index = c->d_seen;
+  a.defer_chase = 0;
+  if (c->h_seen && *reinterpret_cast<volatile uint32_t*>(c->h_seen) &&
+      in_len >= kChaseParallelMin && ensure_chase_scratch(c, in_len) == HZ_OK)
+    a.defer_chase = 1;
   hz_status st = launch(c, K_DECODE_SETUP, s, [&] { return launch_decode_setup(a, c->d_dec, s); });
   if (st != HZ_OK) return st;
+  if (a.defer_chase) {
+    st = launch(c, K_DECODE_CHASE, s,
+                [&] { return launch_decode_chase(a, c->d_dec, c->cs, c->num_sms, s); });
+    if (st != HZ_OK) return st;
+  }
   st = launch(c, K_DECODE, s, [&] {
     return launch_decode_blocks(a, c->d_dec, c->opt_dec_threads, c->num_sms, s);
   });
@@ -509,6 +583,8 @@ static hz_status decompress_host_pipelined(hz_ctx* c, const uint8_t* h_in, uint6
   a.chase_index = c->d_chase;
   a.chase_cap = c->chase_cap;
   a.lut_bits = c->opt_lut_bits;
+  a.seen_no_index = c->d_seen;
+  a.defer_chase = 0;  // the stream has an index
   // the caller's stream may have work on these buffers queued: start after it
   if (cudaEventRecord(c->e_start, s) != cudaSuccess ||
       cudaStreamWaitEvent(c->s_in, c->e_start, 0) != cudaSuccess ||

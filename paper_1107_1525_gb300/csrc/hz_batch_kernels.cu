@@ -89,6 +89,8 @@ __device__ __forceinline__ DecodeArgs decomp_args(const BatchDecomp& d) {
   a.lut_bits = (int)d.lut_bits;
   a.k_begin = 0;
   a.k_end = 0xFFFFFFFFu;
+  a.defer_chase = 0;
+  a.seen_no_index = nullptr;
   return a;
 }
 

@@ -30,7 +30,9 @@ static __device__ __forceinline__ uint32_t e_l0(uint32_t e) { return (e >> 23) &
 constexpr uint32_t kL2Entries = 2048;
 
 struct DecTables {
-  uint32_t ok;          // 1 once the header has been checked
+  uint32_t ok;          // 1 once the header has been checked (and the offsets are known)
+  uint32_t needs_chase; // 1: no stored index, the chase kernel rebuilds the offsets
+  uint32_t minlen;      // shortest code length
   uint32_t flags, B, nb;
   uint64_t n;
   uint64_t blocks_at;   // byte offset of the record area
@@ -52,6 +54,28 @@ static __device__ __forceinline__ uint32_t ld_u32_bytes(const uint8_t* p) {
 
 // ================================================================ setup
 // Parse the header and build the tables (one CTA of 256 threads).
+// The offsets of a stream without a stored index by walking its delimiters,
+// one dependent load per record (the paper's own way, Sec. 2.1): record k
+// starts 1 + ceil(bits / 32) words after record k - 1.  One thread; false
+// (with the error recorded) when the records do not fit the stream.
+static __device__ bool serial_chase(const DecodeArgs& a, uint64_t blocks_at, uint32_t nb) {
+  if (nb > a.chase_cap) {
+    set_error(a.st, HZ_ERR_NOMEM, 0x303);
+    return false;
+  }
+  uint64_t O = 0;
+  for (uint32_t k = 0; k < nb; ++k) {
+    const uint64_t at = blocks_at + 4 * O;
+    if (at + 4 > a.in_len || O > 0xFFFFFFFFull) {
+      set_error(a.st, HZ_ERR_CORRUPT, 0x304);
+      return false;
+    }
+    a.chase_index[k] = (uint32_t)O;
+    O += 1 + ceil32(*reinterpret_cast<const uint32_t*>(a.in + at));
+  }
+  return true;
+}
+
 static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   __shared__ uint32_t s_len[256];
   __shared__ uint8_t s_sorted[256];
@@ -63,6 +87,7 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   const int t = threadIdx.x;
   if (t == 0) {
     T->ok = 0;
+    T->needs_chase = 0;
     a.st->dec_deferred = 0;
     s_ok = a.in_len >= kHeaderBytes;
   }
@@ -271,23 +296,18 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   if (!cap_ok) return;  // uniform
   __syncthreads();
   if (t == 0) {
+    uint32_t minl = 0;
+    for (int k = kMaxLen; k >= 1; --k)
+      if (cnt[k]) minl = (uint32_t)k;
+    T->minlen = minl;
     bool chase_ok = true;
     if (!(flags & kFlagIndex)) {
-      // no stored index: walk the delimiters (one dependent load per block)
-      if (nb > a.chase_cap) {
-        set_error(a.st, HZ_ERR_NOMEM, 0x303);
+      if (a.seen_no_index) *a.seen_no_index = 1u;
+      if (a.defer_chase) {
+        T->needs_chase = 1;  // the chase kernel rebuilds the offsets and sets ok
         chase_ok = false;
-      }
-      uint64_t O = 0;
-      for (uint32_t k = 0; chase_ok && k < nb; ++k) {
-        const uint64_t at = blocks_at + 4 * O;
-        if (at + 4 > a.in_len || O > 0xFFFFFFFFull) {
-          set_error(a.st, HZ_ERR_CORRUPT, 0x304);
-          chase_ok = false;
-          break;
-        }
-        a.chase_index[k] = (uint32_t)O;
-        O += 1 + ceil32(*reinterpret_cast<const uint32_t*>(a.in + at));
+      } else {
+        chase_ok = serial_chase(a, blocks_at, nb);
       }
     }
     if (chase_ok) {

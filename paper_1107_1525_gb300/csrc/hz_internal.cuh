@@ -98,6 +98,7 @@ enum KernelId : int32_t {
   K_DECODE = 6,
   K_DECODE_GENERIC = 7,
   K_BATCH = 8,
+  K_DECODE_CHASE = 9,
   K_COUNT
 };
 
@@ -154,6 +155,9 @@ struct DecodeArgs {
   uint32_t chase_cap;       // capacity of chase_index in entries
   int lut_bits;
   uint32_t k_begin, k_end;  // blocks the fast kernel decodes: [k_begin, min(k_end, nb))
+  // streams without an index: 1 = leave the offset table to the chase kernel
+  uint32_t defer_chase;
+  uint32_t* seen_no_index;  // set to 1 when such a stream is seen (may be null)
 };
 
 // Each returns the cudaError_t of its launch.
