@@ -477,6 +477,7 @@ struct RingWin {
   uint32_t off_w;        // payload word 0 = aligned word off_w
   uint32_t next_slot;    // next slot index (absolute) to request
   uint32_t rw;           // next aligned word to move into the buffer
+  uint32_t nxt;          // that word, read from the ring one fill ahead
   uint32_t bh, bl, nb;
   __device__ __forceinline__ void setup(const uint8_t* payload, const uint8_t* gend,
                                         const uint32_t* my_ring) {
@@ -497,7 +498,9 @@ struct RingWin {
     cp_async16(dst + 16, b1 ? src + 16 : abase, b1);
     cp_async_commit();
   }
-  // start at payload bit `pos` (waits for the first two slots)
+  // Start at payload bit `pos`.  kLongSteps (steps of up to 32 bits, decoder
+  // mode 1): wait for all three slots requested here, else for the first two.
+  template <bool kLongSteps>
   __device__ __forceinline__ void init(uint32_t pos) {
     cp_async_wait<0>();
     const uint32_t A = off_w + (pos >> 5);
@@ -506,25 +509,33 @@ struct RingWin {
     request(h0 + 1);
     request(h0 + 2);
     next_slot = h0 + 3;
-    cp_async_wait<1>();
+    if (kLongSteps) cp_async_wait<0>();
+    else cp_async_wait<1>();
     const uint32_t w0 = ring[A % kRingWords], w1 = ring[(A + 1) % kRingWords];
     const uint32_t r = pos & 31u;
     bh = __funnelshift_l(w1, w0, r);
     bl = w1 << r;
     nb = 64u - r;
     rw = A + 2;
+    nxt = ring[rw % kRingWords];
   }
-  // warp-uniform refill point: the words the next kRefillSteps steps can read
-  // (at most 6, from word rw on) are in slots rw / 8 and the one after; keep
-  // two more requested
+  // Warp-uniform refill point, every kRefillSteps steps; slots up to rw / 8 + 3
+  // are kept requested.  Steps of at most 12 bits read at most 6 words before
+  // the next refill point (7 with the word read ahead), all in slots rw / 8
+  // and the one after: wait for those.  Steps of up to 32 bits (kLongSteps)
+  // read up to 17 (18): wait for every requested slot.
+  template <bool kLongSteps>
   __device__ __forceinline__ void refill() {
     const uint32_t cur = rw / kSlotWords;
     while (next_slot <= cur + 3) request(next_slot++);
-    cp_async_wait<2>();
+    if (kLongSteps) cp_async_wait<0>();
+    else cp_async_wait<2>();
   }
+  // Top the buffer up with the word read ahead, and read the next one: its
+  // shared-memory latency then overlaps the steps before the next fill.
   __device__ __forceinline__ void fill() {
     if (nb <= 32u) {
-      const uint32_t w = ring[rw % kRingWords];
+      const uint32_t w = nxt;
       const uint32_t s = 32u - nb;
       uint32_t lo;
       asm("shl.b32 %0, %1, %2;" : "=r"(lo) : "r"(w), "r"(s));  // 0 for s = 32
@@ -532,6 +543,7 @@ struct RingWin {
       bl |= lo;
       nb += 32u;
       ++rw;
+      nxt = ring[rw % kRingWords];
     }
   }
   __device__ __forceinline__ uint32_t peek(uint32_t W) const { return bh >> (32u - W); }
@@ -654,7 +666,7 @@ __device__ __forceinline__ uint32_t ring_step(const FastShared& sh, RingWin& w, 
   const uint32_t l = ls >> 8;
   bad |= l == 0;
   pos += l ? l : 1u;
-  w.init(pos);
+  w.template init<false>(pos);  // kMode 2: steps through the window stay within W bits
   return ls & 0xFFu;
 }
 
@@ -699,10 +711,10 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
   uint32_t start = my_start, exit_ = my_start, count = 0;
   {
     uint32_t pos = my_start, c = 0;
-    if (active) w.init(pos);
+    if (active) w.template init<kMode == 1>(pos);
     bool dummy = false;
     while (__any_sync(0xFFFFFFFFu, active && pos + W <= my_end)) {
-      if (active) w.refill();
+      if (active) w.template refill<kMode == 1>();
 #pragma unroll 2
       for (uint32_t s = 0; s < kRefillSteps; s += 2) {
         w.fill();  // two steps of at most W <= 12 bits follow
@@ -722,7 +734,7 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
               const uint32_t l = decode_long(sh.c, g.peek64_at(pos)) >> 8;
               pos += l ? l : 1u;
               ++c;
-              w.init(pos);
+              w.template init<kMode == 1>(pos);
             } else {
               const uint32_t nbits = e_nbits(e);
               pos += nbits;
@@ -734,7 +746,7 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
       }
     }
     if (active) {
-      w.refill();
+      w.template refill<kMode == 1>();
       while (pos < my_end) {
         ring_take<kMode>(sh, w, pos, W, g, dummy);
         ++c;
@@ -794,7 +806,7 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
     uint32_t pos = start, rem = active ? v : 0u;
     uint8_t* dst = a.out + (uint64_t)k * sh.c.B + (inc - v);
     if (rem) {
-      w.init(pos);
+      w.template init<kMode == 1>(pos);
       // bytes up to a 16-byte boundary (at most 15 steps: within the slots init awaited)
       while (rem && (((uintptr_t)dst) & 15)) {
         *dst++ = (uint8_t)ring_take<kMode>(sh, w, pos, W, g, bad);
@@ -804,7 +816,7 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
     // 16 symbols per 16-byte store, one refill point per 16 symbols
     while (__any_sync(0xFFFFFFFFu, rem >= 16)) {
       if (rem >= 16) {
-        w.refill();
+        w.template refill<kMode == 1>();
         uint32_t q[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -822,7 +834,7 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
       }
     }
     if (rem) {
-      w.refill();
+      w.template refill<kMode == 1>();
       while (rem) {
         *dst++ = (uint8_t)ring_take<kMode>(sh, w, pos, W, g, bad);
         --rem;
