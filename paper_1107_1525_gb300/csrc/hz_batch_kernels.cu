@@ -236,7 +236,10 @@ __global__ void __launch_bounds__(256) batch_dsetup_kernel(BatchCtl* ctl, BatchD
 }
 
 // Decode units per stream: groups of 8 warps x `per_warp` blocks, sized so a
-// unit holds at least 256 KiB of output (small blocks share a table load).
+// unit holds at least 256 KiB of output (small blocks share a table load) --
+// except in streams of fewer than kDecodeGroupMinBlocks blocks, where every
+// warp takes one block so that the stream spreads over more warps.
+constexpr uint32_t kDecodeGroupMinBlocks = 2048;
 __global__ void __launch_bounds__(1024) batch_dscan_kernel(BatchCtl* ctl, BatchDecomp* decomps) {
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
@@ -251,7 +254,10 @@ __global__ void __launch_bounds__(1024) batch_dscan_kernel(BatchCtl* ctl, BatchD
       BatchDecomp& d = decomps[i];
       const DecTables* T = d.T;
       if (T->ok && T->nb) {
-        const uint32_t per_warp = T->B >= (32u << 10) ? 1u : (32u << 10) / T->B;
+        // a stream with few blocks gives every warp one block (latency); a
+        // long one groups small blocks so that a table load serves 256 KiB
+        const uint32_t per_warp =
+            (T->B >= (32u << 10) || T->nb < kDecodeGroupMinBlocks) ? 1u : (32u << 10) / T->B;
         d.per_warp = per_warp;
         units = (T->nb + 8 * per_warp - 1) / (8 * per_warp);
       }
