@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(1024) batch_dscan_kernel(BatchCtl* ctl, BatchD
 }
 
 // ------------------------------------------------------------- block decoding
-__global__ void __launch_bounds__(kFastThreads) batch_decode_kernel(BatchCtl* ctl,
+__global__ void __launch_bounds__(kFastThreads, 3) batch_decode_kernel(BatchCtl* ctl,
                                                                     const BatchDecomp* decomps) {
   __shared__ FastShared sh;
   __shared__ uint32_t s_u;

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) decode_setup_kernel(DecodeArgs a, DecTabl
   decode_setup_device(a, T);
 }
 
-__global__ void __launch_bounds__(kFastThreads) decode_fast_kernel(DecodeArgs a,
+__global__ void __launch_bounds__(kFastThreads, 3) decode_fast_kernel(DecodeArgs a,
                                                                   const DecTables* T) {
   __shared__ FastShared sh;
   if (!T->ok) return;

@@ -24,6 +24,26 @@ static __device__ __forceinline__ uint32_t e_ns(uint32_t e) { return (e >> 16) &
 static __device__ __forceinline__ uint32_t e_nbits(uint32_t e) { return (e >> 18) & 31u; }
 static __device__ __forceinline__ uint32_t e_l0(uint32_t e) { return (e >> 23) & 15u; }
 
+// Decoder mode 0 (complete code, no code longer than W bits, blocks of at most
+// kFastMaxB symbols) stores another layout, as two 16-bit halves:
+//   low half   bits 0..4  bits taken by every complete code that starts in the
+//                         W-bit window and ends within its first cap bits
+//              bits 8..15 how many codes that is (at least 1)
+//   high half  bits 0..4  length of the first code, bits 8..15 its symbol
+// Bits 5..7 are zero in both halves, so a step can shift the bit buffer by the
+// half itself (funnel shifts use the amount modulo 32) and subtract the whole
+// half from one accumulator whose low byte tracks the buffer's bit count.
+static __host__ __device__ constexpr uint32_t lut0_entry(uint32_t nbits, uint32_t ns, uint32_t l0,
+                                                  uint32_t s0) {
+  return nbits | (ns << 8) | ((l0 | (s0 << 8)) << 16);
+}
+// The mode-0 entry of value v sits at lut0_pos(v): bits 5..9 of v folded into
+// the bank bits, since v's low bits are the start of the next code, which
+// repeats across lanes (long codes share their leading ones) and would pile
+// the lanes' lookups onto a few shared-memory banks.  A bijection on [0, 2^W).
+static __host__ __device__ constexpr uint32_t lut0_pos(uint32_t v) { return v ^ ((v >> 5) & 31u); }
+constexpr uint32_t kFastMaxB = 65536;  // larger blocks go to the generic kernel
+
 // Second-level table entries: codes longer than W bits whose W-bit prefixes
 // have at most this many continuations in all; larger code sets take the
 // per-length search.
@@ -38,6 +58,8 @@ struct DecTables {
   uint64_t blocks_at;   // byte offset of the record area
   uint32_t maxlen, lut_bits;
   uint32_t complete;            // Kraft sum exactly 1: every bit string decodes
+  uint32_t fill_k;              // mode 0: lut holds the mode-0 layout; steps per buffer fill
+                                // of the output pass (2, 3 or 4); 0: the general layout
   uint32_t cnt[kMaxLen + 1];
   uint32_t offs[kMaxLen + 1];   // position in sorted[] of the first code of each length
   uint64_t first[kMaxLen + 1];  // first canonical code of each length
@@ -83,7 +105,7 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   __shared__ uint64_t first[kMaxLen + 1];
   __shared__ uint32_t offs[kMaxLen + 1];
   __shared__ int s_ok;
-  __shared__ uint32_t s_maxlen;
+  __shared__ uint32_t s_maxlen, s_complete;
   const int t = threadIdx.x;
   if (t == 0) {
     T->ok = 0;
@@ -140,6 +162,7 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
     if (!kraft || (n > 0 && nsym == 0)) s_ok = 0;
     s_maxlen = maxl;
     T->complete = hi == 1 && lo == 0;
+    s_complete = hi == 1 && lo == 0;
   }
   __syncthreads();
   if (!s_ok) {
@@ -213,11 +236,25 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
     s_t1[v] = e1;
   }
   __syncthreads();
+  // Mode 0: every W-bit value starts a code of at most W bits.  The counting
+  // pass's steps then take all the codes that end within cap bits: 10 when no
+  // code is longer (so that three steps follow one buffer fill), else W.
+  const bool mode0 = s_complete && maxl <= (uint32_t)W && B <= kFastMaxB;
+  const uint32_t cap = maxl <= 10 ? ((uint32_t)W < 10u ? (uint32_t)W : 10u) : (uint32_t)W;
   for (uint32_t v = t * per; v < (t + 1) * per && v < nv; ++v) {
     const uint32_t e1 = s_t1[v];
     const uint32_t l0 = e1 >> 8, s0 = e1 & 0xFFu;
     uint32_t e = 0, ext = 0;
-    if (l0) {
+    if (mode0) {
+      uint32_t used = l0, ns = 1;
+      for (;;) {
+        const uint32_t l = s_t1[(v << used) & (nv - 1)] >> 8;  // >= 1: the code is complete
+        if (used + l > cap) break;
+        used += l;
+        ++ns;
+      }
+      e = lut0_entry(used, ns, l0, s0);
+    } else if (l0) {
       // the next code, when it fits in the W - l0 bits that follow
       const uint32_t e2 = l0 < (uint32_t)W ? s_t1[(v << l0) & (nv - 1)] : 0u;
       const uint32_t l1 = e2 >> 8;
@@ -233,7 +270,7 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
       my_l2 += ext ? (1u << ext) : 0u;
     }
     s_ext[v] = (uint8_t)ext;
-    T->lut[v] = e;
+    T->lut[mode0 ? lut0_pos(v) : v] = e;
   }
   s_part[t] = my_l2;
   __syncthreads();
@@ -288,6 +325,7 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
     T->blocks_at = blocks_at;
     T->maxlen = maxl;
     T->lut_bits = (uint32_t)W;
+    T->fill_k = mode0 ? (maxl <= 8 ? 4u : maxl <= 10 ? 3u : 2u) : 0u;
     *a.out_len = n;
     if (!cap_ok) set_error(a.st, HZ_ERR_CAPACITY, 0x302);
     // blocks too large for the fast kernel all go to the generic one
@@ -404,7 +442,6 @@ static __device__ __forceinline__ RecInfo read_record(const DecodeArgs& a, const
 // of the payload; ranges of ~2000 symbols make the resynchronisation (tens of
 // bits) negligible, and every step after the table lookup is warp-local.
 constexpr int kFastThreads = 256;
-constexpr uint32_t kFastMaxB = 65536;  // larger blocks go to the generic kernel
 
 static __host__ __device__ __forceinline__ bool fast_block_size(uint32_t B) { return B <= kFastMaxB; }
 
@@ -428,7 +465,7 @@ constexpr uint32_t kRefillSteps = 16;
 struct FastShared {
   uint32_t lut[1 << kLutMaxBits];
   uint16_t l2[kL2Entries];
-  uint32_t has_l2;
+  uint32_t has_l2, fill_k;
   CanonTables c;
   __align__(16) uint32_t ring[kFastThreads * kRingStride];
 };
@@ -444,7 +481,10 @@ static __device__ __forceinline__ void load_fast_tables(FastShared& sh, const De
     uint32_t* dst = reinterpret_cast<uint32_t*>(sh.l2);
     for (int i = tid; i < (int)(kL2Entries / 2); i += nt) dst[i] = src[i];
   }
-  if (tid == 0) sh.has_l2 = has_l2;
+  if (tid == 0) {
+    sh.has_l2 = has_l2;
+    sh.fill_k = T->fill_k;
+  }
   load_canon(sh.c, T, tid, nt);
 }
 
@@ -479,6 +519,7 @@ struct RingWin {
   uint32_t rw;           // next aligned word to move into the buffer
   uint32_t nxt;          // that word, read from the ring one fill ahead
   uint32_t bh, bl, nb;
+  uint32_t nacc;         // mode 0: nb = (32 * rw + nacc) mod 256
   __device__ __forceinline__ void setup(const uint8_t* payload, const uint8_t* gend,
                                         const uint32_t* my_ring) {
     abase = reinterpret_cast<const uint8_t*>(((uintptr_t)payload) & ~(uintptr_t)15);
@@ -555,6 +596,31 @@ struct RingWin {
   }
   // the buffer as 64 bits, MSB first (valid for the next nb bits)
   __device__ __forceinline__ uint64_t peek64() const { return ((uint64_t)bh << 32) | bl; }
+  // ---- mode 0.  The bit count is implicit: nb = (32 * rw + nacc) mod 256.  A
+  // step consumes the low 5 bits of a table half and subtracts the whole half
+  // from nacc; what the half holds above bit 7 drops out of the low byte.
+  __device__ __forceinline__ void init0(uint32_t pos) {
+    init<false>(pos);
+    nacc = nb - 32u * rw;
+  }
+  __device__ __forceinline__ uint32_t nb0() const { return (32u * rw + nacc) & 255u; }
+  // the payload bit position of the next unread bit
+  __device__ __forceinline__ uint32_t pos0() const { return 32u * (rw - off_w) - nb0(); }
+  // a word into the buffer when it holds at most 32 bits (after it, more than 32)
+  __device__ __forceinline__ void fill0() {
+    const uint32_t n = nb0();
+    if (n <= 32u) {
+      bh |= __funnelshift_rc(nxt, 0u, n);  // nxt >> n
+      bl |= __funnelshift_rc(0u, nxt, n);  // nxt << (32 - n)
+      ++rw;
+      nxt = ring[rw % kRingWords];
+    }
+  }
+  __device__ __forceinline__ void take0(uint32_t h) {
+    bh = __funnelshift_l(bl, bh, h);
+    bl = __funnelshift_l(0u, bl, h);
+    nacc -= h;
+  }
   // l <= 32 <= nb (a code of up to 32 bits, right after a fill)
   __device__ __forceinline__ void consume_long(uint32_t l) {
     uint32_t lo;
@@ -846,16 +912,204 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
   if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x322);
 }
 
+// ---------------------------------------------------------------- mode 0
+// The same three phases as decode_block_warp, for codes that all fit the
+// table (every W-bit value starts one) and the mode-0 table layout.  The
+// counting pass takes every code that ends within cap bits in one step (cap:
+// 10 for K1 = 3, W for K1 = 2) and fills the buffer every K1 steps; the output
+// pass takes one code per step and fills every K2 steps (codes of at most
+// 32 / K2 bits).  A fill leaves more than 32 bits in the buffer as long as it
+// held at least one, so K steps of at most c bits with K * c <= 32 keep at
+// least c bits in it for every step's lookup (an entry depends on its first
+// c bits only).  While a lane is more than a refill period's worth of steps
+// from the end of its range, its steps run without a bounds check.
+static __device__ __forceinline__ uint32_t lut0_lo(const FastShared& sh, uint32_t v) {
+  return reinterpret_cast<const uint16_t*>(sh.lut)[2 * lut0_pos(v)];
+}
+static __device__ __forceinline__ uint32_t lut0_hi(const FastShared& sh, uint32_t v) {
+  return reinterpret_cast<const uint16_t*>(sh.lut)[2 * lut0_pos(v) + 1];
+}
+// one code from the plain reader (the fix-up): advance pos by its length
+static __device__ __forceinline__ void skip_symbol0(const FastShared& sh, GWin& g, uint32_t& pos,
+                                                    uint32_t sW) {
+  pos += lut0_hi(sh, g.peek(pos) >> sW) & 31u;
+  g.step(pos);
+}
+
+template <int K1, int K2>
+__device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t k) {
+  constexpr uint32_t kCap = K1 == 3 ? 10u : (uint32_t)kLutMaxBits;  // bits per counting step
+  constexpr uint32_t kG1 = K1 == 3 ? 15u : 16u;                      // counting steps per refill
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t sW = 32u - sh.c.W;
+  RecInfo r;
+  if (lane == 0) r = read_record(a, sh.c, k);
+  r.rec = __shfl_sync(0xFFFFFFFFu, r.rec, 0);
+  r.bits = __shfl_sync(0xFFFFFFFFu, r.bits, 0);
+  r.nw = __shfl_sync(0xFFFFFFFFu, r.nw, 0);
+  r.cnt_k = __shfl_sync(0xFFFFFFFFu, r.cnt_k, 0);
+  r.ok = __shfl_sync(0xFFFFFFFFu, (int)r.ok, 0);
+  if (!r.ok) {
+    if (lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x320);
+    return;
+  }
+  const uint32_t bits = r.bits, nw = r.nw;
+  const uint8_t* payload = a.in + r.rec + 4;
+  GWin g;
+  g.p = reinterpret_cast<const uint32_t*>(payload);
+  g.nw = nw;
+  RingWin w;
+  w.setup(payload, a.in + a.in_len, sh.ring + threadIdx.x * kRingStride);
+  const uint32_t Lw = (nw + 31) / 32;
+  const uint32_t L = Lw * 32;
+  const uint32_t nsub = (bits + L - 1) / L;
+  const bool active = lane < nsub;
+  const uint32_t my_start = lane * L;
+  const uint32_t my_end = active ? min(my_start + L, bits) : 0u;
+
+  // ---- pass 1: speculative count of the codes that start in my range
+  uint32_t start = my_start, exit_ = my_start, count = 0;
+  if (active) {
+    w.init0(my_start);
+    const uint32_t nacc0 = w.nacc;
+    // far from the end: kG1 steps of at most kCap bits, unchecked
+    while (w.pos0() + kG1 * kCap <= my_end) {
+      w.refill<false>();
+#pragma unroll
+      for (uint32_t s = 0; s < kG1; ++s) {
+        if (s % K1 == 0) w.fill0();
+        w.take0(lut0_lo(sh, w.bh >> sW));
+      }
+    }
+    // near it: steps while all their codes start before the end
+    w.refill<false>();
+    for (;;) {
+      w.fill0();
+      if (w.pos0() + kCap > my_end) break;
+      w.take0(lut0_lo(sh, w.bh >> sW));
+    }
+    // then one code at a time (counted as 256 in nacc, like a step's count)
+    uint32_t pos = w.pos0();
+    while (pos < my_end) {
+      w.fill0();
+      const uint32_t l = lut0_hi(sh, w.bh >> sW) & 31u;
+      w.take0(l | 256u);
+      pos += l;
+    }
+    exit_ = pos;
+    count = ((nacc0 - w.nacc) - (pos - my_start)) >> 8;
+  }
+  // ---- fix-up: restart each range at its left neighbour's exit until all agree
+  for (uint32_t round = 0; round <= 32; ++round) {
+    const uint32_t want = __shfl_up_sync(0xFFFFFFFFu, exit_, 1);
+    const bool mismatch = active && lane > 0 && want != start;
+    if (!__any_sync(0xFFFFFFFFu, mismatch)) break;
+    if (mismatch) {
+      uint32_t pa = want, pb = start, ca = 0, cb = 0;
+      GWin wa = g, wb = g;
+      wa.init(pa);
+      wb.init(pb);
+      while (pa != pb && (pa < my_end || pb < my_end)) {
+        if (pa < pb) {
+          skip_symbol0(sh, wa, pa, sW);
+          ++ca;
+        } else {
+          skip_symbol0(sh, wb, pb, sW);
+          ++cb;
+        }
+      }
+      if (pa == pb) {
+        count = count - cb + ca;
+      } else {
+        exit_ = pa;
+        count = ca;
+      }
+      start = want;
+    }
+  }
+  // ---- exclusive scan of the counts
+  const uint32_t v = active ? count : 0u;
+  uint32_t inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+    if (lane >= (uint32_t)d) inc += o;
+  }
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+  const uint32_t last_exit = __shfl_sync(0xFFFFFFFFu, exit_, nsub - 1);
+  if (total != r.cnt_k || last_exit != bits) {
+    if (lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x321);
+    cp_async_wait<0>();
+    return;  // uniform
+  }
+  // ---- pass 2: decode from the true boundary and store the symbols
+  bool bad = false;
+  {
+    uint32_t rem = active ? v : 0u;
+    uint8_t* dst = a.out + (uint64_t)k * sh.c.B + (inc - v);
+    if (rem) {
+      w.init0(start);
+      // bytes up to a 16-byte boundary (at most 15 steps: within the slots init awaited)
+      while (rem && (((uintptr_t)dst) & 15)) {
+        w.fill0();
+        const uint32_t h = lut0_hi(sh, w.bh >> sW);
+        w.take0(h);
+        *dst++ = (uint8_t)(h >> 8);
+        --rem;
+      }
+    }
+    // 16 symbols per 16-byte store, one refill point per 16 symbols
+    while (__any_sync(0xFFFFFFFFu, rem >= 16)) {
+      if (rem >= 16) {
+        w.refill<false>();
+        uint32_t q[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint32_t word = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            if ((4 * j + b) % K2 == 0) w.fill0();
+            const uint32_t h = lut0_hi(sh, w.bh >> sW);
+            w.take0(h);
+            // byte b of the word <- the symbol (byte 1 of h)
+            word = __byte_perm(word, h, b == 0 ? 0x3215u : b == 1 ? 0x3250u : b == 2 ? 0x3510u : 0x5210u);
+          }
+          q[j] = word;
+        }
+        *reinterpret_cast<uint4*>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
+        dst += 16;
+        rem -= 16;
+      }
+    }
+    if (rem) {
+      w.refill<false>();
+      while (rem) {
+        w.fill0();
+        const uint32_t h = lut0_hi(sh, w.bh >> sW);
+        w.take0(h);
+        *dst++ = (uint8_t)(h >> 8);
+        --rem;
+      }
+    }
+    if (active && v) bad = w.pos0() != exit_;
+  }
+  cp_async_wait<0>();  // nothing of this block may land in the ring after we leave
+  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x322);
+}
+
 // The decoder mode for the tables (see RingWin), and one block in that mode.
 static __device__ __forceinline__ int fast_mode(const DecTables* T, const CanonTables& c) {
-  if (T->complete && c.maxlen <= c.W) return 0;  // every code fits the table: no escapes
+  if (T->fill_k) return 0;  // every code fits the table: no escapes
   return c.maxlen <= 32 ? 1 : 2;
 }
 
 static __device__ __forceinline__ void decode_block_fast(const DecodeArgs& a, FastShared& sh,
                                                          uint32_t k, int mode) {
-  if (mode == 0) decode_block_warp<0>(a, sh, k);
-  else if (mode == 1) decode_block_warp<1>(a, sh, k);
+  if (mode == 0) {
+    if (sh.fill_k == 4) decode_block_warp0<3, 4>(a, sh, k);
+    else if (sh.fill_k == 3) decode_block_warp0<3, 3>(a, sh, k);
+    else decode_block_warp0<2, 2>(a, sh, k);
+  } else if (mode == 1) decode_block_warp<1>(a, sh, k);
   else decode_block_warp<2>(a, sh, k);
 }
 
