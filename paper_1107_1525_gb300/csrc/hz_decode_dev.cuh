@@ -488,8 +488,11 @@ static __device__ __forceinline__ void load_fast_tables(FastShared& sh, const De
   load_canon(sh.c, T, tid, nt);
 }
 
+// (.cg: the payload goes to shared memory through L2 only; allocating it in L1
+// as well costs data-pipe wavefronts and L1 room for nothing, since a lane
+// reads its slots once per pass)
 static __device__ __forceinline__ void cp_async16(uint32_t smem_addr, const void* gptr, uint32_t bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr), "l"(gptr),
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr), "l"(gptr),
                "r"(bytes)
                : "memory");
 }
@@ -932,7 +935,8 @@ static __device__ __forceinline__ uint32_t lut0_hi(const FastShared& sh, uint32_
 // one code from the plain reader (the fix-up): advance pos by its length
 static __device__ __forceinline__ void skip_symbol0(const FastShared& sh, GWin& g, uint32_t& pos,
                                                     uint32_t sW) {
-  pos += lut0_hi(sh, g.peek(pos) >> sW) & 31u;
+  const uint32_t l = lut0_hi(sh, g.peek(pos) >> sW) & 31u;
+  pos += l ? l : 1u;  // >= 1 in a mode-0 table; never stall on a bad one
   g.step(pos);
 }
 
@@ -969,11 +973,16 @@ __device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t
 
   // ---- pass 1: speculative count of the codes that start in my range
   uint32_t start = my_start, exit_ = my_start, count = 0;
+  bool stalled = false;
   if (active) {
     w.init0(my_start);
     const uint32_t nacc0 = w.nacc;
+    // Every step of a mode-0 table takes at least one bit, so a range of L
+    // bits needs at most L steps; the budget only guards against a bad table.
+    uint32_t budget = my_end - my_start + 2 * kCap;
     // far from the end: kG1 steps of at most kCap bits, unchecked
-    while (w.pos0() + kG1 * kCap <= my_end) {
+    while (w.pos0() + kG1 * kCap <= my_end && budget >= kG1) {
+      budget -= kG1;
       w.refill<false>();
 #pragma unroll
       for (uint32_t s = 0; s < kG1; ++s) {
@@ -983,21 +992,27 @@ __device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t
     }
     // near it: steps while all their codes start before the end
     w.refill<false>();
-    for (;;) {
+    for (; budget; --budget) {
       w.fill0();
       if (w.pos0() + kCap > my_end) break;
       w.take0(lut0_lo(sh, w.bh >> sW));
     }
     // then one code at a time (counted as 256 in nacc, like a step's count)
     uint32_t pos = w.pos0();
-    while (pos < my_end) {
+    for (; pos < my_end && budget; --budget) {
       w.fill0();
       const uint32_t l = lut0_hi(sh, w.bh >> sW) & 31u;
       w.take0(l | 256u);
       pos += l;
     }
+    stalled = pos < my_end;
     exit_ = pos;
     count = ((nacc0 - w.nacc) - (pos - my_start)) >> 8;
+  }
+  if (__any_sync(0xFFFFFFFFu, stalled)) {
+    if (lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x323);
+    cp_async_wait<0>();
+    return;  // uniform
   }
   // ---- fix-up: restart each range at its left neighbour's exit until all agree
   for (uint32_t round = 0; round <= 32; ++round) {
