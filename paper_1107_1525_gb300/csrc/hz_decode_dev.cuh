@@ -37,7 +37,12 @@ static __host__ __device__ constexpr uint32_t lut0_entry(uint32_t nbits, uint32_
                                                   uint32_t s0) {
   return nbits | (ns << 8) | ((l0 | (s0 << 8)) << 16);
 }
-// The mode-0 entry of value v sits at lut0_pos(v): bits 5..9 of v folded into
+// When no code is longer than 10 bits (and W >= 10) every entry is fixed by the
+// top 10 bits, and shared memory holds 8 interleaved copies of that 1024-entry
+// table: entry u of copy c (c = lane mod 8) is word 8u + c, so the lanes that
+// share a copy (lane, lane + 8, lane + 16, lane + 24) spread over banks c,
+// c+8, c+16, c+24 (about 2 wavefronts per lookup instead of about 3.5).
+// Otherwise the mode-0 entry of value v sits at lut0_pos(v): bits 5..9 of v folded into
 // the bank bits, since v's low bits are the start of the next code, which
 // repeats across lanes (long codes share their leading ones) and would pile
 // the lanes' lookups onto a few shared-memory banks.  A bijection on [0, 2^W).
@@ -60,6 +65,8 @@ struct DecTables {
   uint32_t complete;            // Kraft sum exactly 1: every bit string decodes
   uint32_t fill_k;              // mode 0: lut holds the mode-0 layout; steps per buffer fill
                                 // of the output pass (2, 3 or 4); 0: the general layout
+  uint32_t lut_rep;             // mode 0, no code longer than 10 bits, W >= 10: lut[0, 1024)
+                                // is indexed by the top 10 bits, kept 8 times in shared memory
   uint32_t cnt[kMaxLen + 1];
   uint32_t offs[kMaxLen + 1];   // position in sorted[] of the first code of each length
   uint64_t first[kMaxLen + 1];  // first canonical code of each length
@@ -240,12 +247,15 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   // pass's steps then take all the codes that end within cap bits: 10 when no
   // code is longer (so that three steps follow one buffer fill), else W.
   const bool mode0 = s_complete && maxl <= (uint32_t)W && B <= kFastMaxB;
-  const uint32_t cap = maxl <= 10 ? ((uint32_t)W < 10u ? (uint32_t)W : 10u) : (uint32_t)W;
+  const bool rep = mode0 && maxl <= 10 && W >= 10;
+  const uint32_t cap = rep ? 10u : (uint32_t)W;
   for (uint32_t v = t * per; v < (t + 1) * per && v < nv; ++v) {
     const uint32_t e1 = s_t1[v];
     const uint32_t l0 = e1 >> 8, s0 = e1 & 0xFFu;
     uint32_t e = 0, ext = 0;
-    if (mode0) {
+    if (rep) {
+      // the 10-bit table is built below
+    } else if (mode0) {
       uint32_t used = l0, ns = 1;
       for (;;) {
         const uint32_t l = s_t1[(v << used) & (nv - 1)] >> 8;  // >= 1: the code is complete
@@ -270,7 +280,22 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
       my_l2 += ext ? (1u << ext) : 0u;
     }
     s_ext[v] = (uint8_t)ext;
-    T->lut[mode0 ? lut0_pos(v) : v] = e;
+    if (!rep) T->lut[mode0 ? lut0_pos(v) : v] = e;
+  }
+  if (rep) {
+    for (uint32_t u = t; u < 1024u; u += blockDim.x) {
+      const uint32_t v = u << (W - 10);  // the W-bit value with u on top
+      const uint32_t e1 = s_t1[v];
+      const uint32_t l0 = e1 >> 8;       // <= 10: fixed by u
+      uint32_t used = l0, ns = 1;
+      for (;;) {
+        const uint32_t l = s_t1[(v << used) & (nv - 1)] >> 8;
+        if (used + l > cap) break;
+        used += l;
+        ++ns;
+      }
+      T->lut[u] = lut0_entry(used, ns, l0, e1 & 0xFFu);
+    }
   }
   s_part[t] = my_l2;
   __syncthreads();
@@ -315,7 +340,7 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
       T->l2[i] = k ? (uint16_t)(sym | (k << 8)) : (uint16_t)0;
     }
   }
-  if (t == 0) T->has_l2 = l2_ok ? 1u : 0u;
+  if (t == 0) T->has_l2 = l2_ok && !mode0 ? 1u : 0u;
   const bool cap_ok = n <= a.out_cap;
   if (t == 0) {
     T->flags = flags;
@@ -325,7 +350,8 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
     T->blocks_at = blocks_at;
     T->maxlen = maxl;
     T->lut_bits = (uint32_t)W;
-    T->fill_k = mode0 ? (maxl <= 8 ? 4u : maxl <= 10 ? 3u : 2u) : 0u;
+    T->fill_k = mode0 ? (rep ? (maxl <= 8 ? 4u : 3u) : 2u) : 0u;
+    T->lut_rep = rep ? 1u : 0u;
     *a.out_len = n;
     if (!cap_ok) set_error(a.st, HZ_ERR_CAPACITY, 0x302);
     // blocks too large for the fast kernel all go to the generic one
@@ -462,10 +488,14 @@ constexpr uint32_t kRingWords = kSlotWords * kRingSlots;
 constexpr uint32_t kRingStride = kRingWords + 4;  // words between lanes' rings (16-byte aligned)
 constexpr uint32_t kRefillSteps = 16;
 
+// Table area: the first-level table (words [0, 2^W)) and the second-level one
+// (from word 4096), or the 8 copies of the 10-bit mode-0 table.
+constexpr uint32_t kFastLutWords = 8192;
+static_assert((1u << kLutMaxBits) + kL2Entries / 2 <= kFastLutWords, "table area");
+
 struct FastShared {
-  uint32_t lut[1 << kLutMaxBits];
-  uint16_t l2[kL2Entries];
-  uint32_t has_l2, fill_k;
+  uint32_t lut[kFastLutWords];
+  uint32_t has_l2, fill_k, lut_rep;
   CanonTables c;
   __align__(16) uint32_t ring[kFastThreads * kRingStride];
 };
@@ -474,16 +504,22 @@ struct FastShared {
 static __device__ __forceinline__ void load_fast_tables(FastShared& sh, const DecTables* T,
                                                         int tid, int nt) {
   const int W = (int)T->lut_bits;
-  for (int i = tid; i < (1 << W); i += nt) sh.lut[i] = T->lut[i];
-  const uint32_t has_l2 = T->has_l2;
+  const uint32_t lut_rep = T->lut_rep;
+  if (lut_rep) {
+    for (int i = tid; i < (int)kFastLutWords; i += nt) sh.lut[i] = T->lut[i >> 3];
+  } else {
+    for (int i = tid; i < (1 << W); i += nt) sh.lut[i] = T->lut[i];
+  }
+  // (the replicated table fills the whole area; mode 0 needs no second level)
+  const uint32_t has_l2 = lut_rep ? 0u : T->has_l2;
   if (has_l2) {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(T->l2);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(sh.l2);
-    for (int i = tid; i < (int)(kL2Entries / 2); i += nt) dst[i] = src[i];
+    for (int i = tid; i < (int)(kL2Entries / 2); i += nt) sh.lut[(1 << kLutMaxBits) + i] = src[i];
   }
   if (tid == 0) {
     sh.has_l2 = has_l2;
     sh.fill_k = T->fill_k;
+    sh.lut_rep = lut_rep;
   }
   load_canon(sh.c, T, tid, nt);
 }
@@ -703,7 +739,8 @@ static __device__ __forceinline__ uint32_t long_code(const FastShared& sh, uint3
   if (sh.has_l2) {
     const uint32_t ext = e_nbits(e);
     if (!ext) return 0u;  // no code starts with these W bits
-    return sh.l2[(e & 0xFFFFu) + (uint32_t)((v64 << W) >> (64 - ext))];
+    const uint16_t* l2 = reinterpret_cast<const uint16_t*>(sh.lut + (1 << kLutMaxBits));
+    return l2[(e & 0xFFFFu) + (uint32_t)((v64 << W) >> (64 - ext))];
   }
   return decode_long(sh.c, v64);
 }
@@ -919,33 +956,43 @@ __device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t 
 // The same three phases as decode_block_warp, for codes that all fit the
 // table (every W-bit value starts one) and the mode-0 table layout.  The
 // counting pass takes every code that ends within cap bits in one step (cap:
-// 10 for K1 = 3, W for K1 = 2) and fills the buffer every K1 steps; the output
+// 10 (or W if smaller) and K1 = 3 when no code is longer, else W and K1 = 2)
+// and fills the buffer every K1 steps; the output
 // pass takes one code per step and fills every K2 steps (codes of at most
 // 32 / K2 bits).  A fill leaves more than 32 bits in the buffer as long as it
 // held at least one, so K steps of at most c bits with K * c <= 32 keep at
 // least c bits in it for every step's lookup (an entry depends on its first
 // c bits only).  While a lane is more than a refill period's worth of steps
 // from the end of its range, its steps run without a bounds check.
-static __device__ __forceinline__ uint32_t lut0_lo(const FastShared& sh, uint32_t v) {
-  return reinterpret_cast<const uint16_t*>(sh.lut)[2 * lut0_pos(v)];
+// The 16-bit index of the entry's low half for a bit buffer whose top 32 bits
+// are `top` (c2: twice the lane's copy, for the replicated table).
+template <bool kRep>
+static __device__ __forceinline__ uint32_t lut0_at(uint32_t top, uint32_t sW, uint32_t c2) {
+  if (kRep) return ((top >> 22) << 4) | c2;  // word 8u + c
+  return lut0_pos(top >> sW) << 1;
 }
-static __device__ __forceinline__ uint32_t lut0_hi(const FastShared& sh, uint32_t v) {
-  return reinterpret_cast<const uint16_t*>(sh.lut)[2 * lut0_pos(v) + 1];
+static __device__ __forceinline__ uint32_t lut0_lo(const FastShared& sh, uint32_t i) {
+  return reinterpret_cast<const uint16_t*>(sh.lut)[i];
+}
+static __device__ __forceinline__ uint32_t lut0_hi(const FastShared& sh, uint32_t i) {
+  return reinterpret_cast<const uint16_t*>(sh.lut)[i + 1];
 }
 // one code from the plain reader (the fix-up): advance pos by its length
+template <bool kRep>
 static __device__ __forceinline__ void skip_symbol0(const FastShared& sh, GWin& g, uint32_t& pos,
-                                                    uint32_t sW) {
-  const uint32_t l = lut0_hi(sh, g.peek(pos) >> sW) & 31u;
+                                                    uint32_t sW, uint32_t c2) {
+  const uint32_t l = lut0_hi(sh, lut0_at<kRep>(g.peek(pos), sW, c2)) & 31u;
   pos += l ? l : 1u;  // >= 1 in a mode-0 table; never stall on a bad one
   g.step(pos);
 }
 
-template <int K1, int K2>
+template <int K1, int K2, bool kRep>
 __device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t k) {
   constexpr uint32_t kCap = K1 == 3 ? 10u : (uint32_t)kLutMaxBits;  // bits per counting step
   constexpr uint32_t kG1 = K1 == 3 ? 15u : 16u;                      // counting steps per refill
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t sW = 32u - sh.c.W;
+  const uint32_t c2 = (lane & 7u) << 1;
   RecInfo r;
   if (lane == 0) r = read_record(a, sh.c, k);
   r.rec = __shfl_sync(0xFFFFFFFFu, r.rec, 0);
@@ -987,7 +1034,7 @@ __device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t
 #pragma unroll
       for (uint32_t s = 0; s < kG1; ++s) {
         if (s % K1 == 0) w.fill0();
-        w.take0(lut0_lo(sh, w.bh >> sW));
+        w.take0(lut0_lo(sh, lut0_at<kRep>(w.bh, sW, c2)));
       }
     }
     // near it: steps while all their codes start before the end
@@ -995,13 +1042,13 @@ __device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t
     for (; budget; --budget) {
       w.fill0();
       if (w.pos0() + kCap > my_end) break;
-      w.take0(lut0_lo(sh, w.bh >> sW));
+      w.take0(lut0_lo(sh, lut0_at<kRep>(w.bh, sW, c2)));
     }
     // then one code at a time (counted as 256 in nacc, like a step's count)
     uint32_t pos = w.pos0();
     for (; pos < my_end && budget; --budget) {
       w.fill0();
-      const uint32_t l = lut0_hi(sh, w.bh >> sW) & 31u;
+      const uint32_t l = lut0_hi(sh, lut0_at<kRep>(w.bh, sW, c2)) & 31u;
       w.take0(l | 256u);
       pos += l;
     }
@@ -1026,10 +1073,10 @@ __device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t
       wb.init(pb);
       while (pa != pb && (pa < my_end || pb < my_end)) {
         if (pa < pb) {
-          skip_symbol0(sh, wa, pa, sW);
+          skip_symbol0<kRep>(sh, wa, pa, sW, c2);
           ++ca;
         } else {
-          skip_symbol0(sh, wb, pb, sW);
+          skip_symbol0<kRep>(sh, wb, pb, sW, c2);
           ++cb;
         }
       }
@@ -1067,7 +1114,7 @@ __device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t
       // bytes up to a 16-byte boundary (at most 15 steps: within the slots init awaited)
       while (rem && (((uintptr_t)dst) & 15)) {
         w.fill0();
-        const uint32_t h = lut0_hi(sh, w.bh >> sW);
+        const uint32_t h = lut0_hi(sh, lut0_at<kRep>(w.bh, sW, c2));
         w.take0(h);
         *dst++ = (uint8_t)(h >> 8);
         --rem;
@@ -1084,7 +1131,7 @@ __device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             if ((4 * j + b) % K2 == 0) w.fill0();
-            const uint32_t h = lut0_hi(sh, w.bh >> sW);
+            const uint32_t h = lut0_hi(sh, lut0_at<kRep>(w.bh, sW, c2));
             w.take0(h);
             // byte b of the word <- the symbol (byte 1 of h)
             word = __byte_perm(word, h, b == 0 ? 0x3215u : b == 1 ? 0x3250u : b == 2 ? 0x3510u : 0x5210u);
@@ -1100,7 +1147,7 @@ __device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t
       w.refill<false>();
       while (rem) {
         w.fill0();
-        const uint32_t h = lut0_hi(sh, w.bh >> sW);
+        const uint32_t h = lut0_hi(sh, lut0_at<kRep>(w.bh, sW, c2));
         w.take0(h);
         *dst++ = (uint8_t)(h >> 8);
         --rem;
@@ -1121,9 +1168,9 @@ static __device__ __forceinline__ int fast_mode(const DecTables* T, const CanonT
 static __device__ __forceinline__ void decode_block_fast(const DecodeArgs& a, FastShared& sh,
                                                          uint32_t k, int mode) {
   if (mode == 0) {
-    if (sh.fill_k == 4) decode_block_warp0<3, 4>(a, sh, k);
-    else if (sh.fill_k == 3) decode_block_warp0<3, 3>(a, sh, k);
-    else decode_block_warp0<2, 2>(a, sh, k);
+    if (sh.fill_k == 4) decode_block_warp0<3, 4, true>(a, sh, k);
+    else if (sh.fill_k == 3) decode_block_warp0<3, 3, true>(a, sh, k);
+    else decode_block_warp0<2, 2, false>(a, sh, k);
   } else if (mode == 1) decode_block_warp<1>(a, sh, k);
   else decode_block_warp<2>(a, sh, k);
 }
