@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(1024) batch_dscan_kernel(BatchCtl* ctl, BatchD
 // ------------------------------------------------------------- block decoding
 __global__ void __launch_bounds__(kFastThreads, 3) batch_decode_kernel(BatchCtl* ctl,
                                                                     const BatchDecomp* decomps) {
-  __shared__ FastShared sh;
+  FastShared& sh = g_fast;
   __shared__ uint32_t s_u;
   const uint32_t nunits = ctl->dec_units, n = ctl->ndecomp;
   uint32_t cur = 0xFFFFFFFFu;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) batch_decode_kernel(BatchCtl*
     for (uint32_t j = 0; j < d.per_warp; ++j) {
       const uint32_t k = k0 + j;
       if (k >= sh.c.nb) break;
-      decode_block_fast(a, sh, k, mode);
+      decode_block_fast(a, k, mode);
     }
   }
 }

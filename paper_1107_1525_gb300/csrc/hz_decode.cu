@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) decode_setup_kernel(DecodeArgs a, DecTabl
 
 __global__ void __launch_bounds__(kFastThreads, 3) decode_fast_kernel(DecodeArgs a,
                                                                   const DecTables* T) {
-  __shared__ FastShared sh;
+  FastShared& sh = g_fast;
   if (!T->ok) return;
   if (!fast_block_size(T->B)) return;  // every block goes to the generic kernel
   load_fast_tables(sh, T, threadIdx.x, kFastThreads);
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) decode_fast_kernel(DecodeArgs
   const int mode = fast_mode(T, sh.c);
   const uint32_t k_end = a.k_end < sh.c.nb ? a.k_end : sh.c.nb;
   for (uint32_t k = a.k_begin + blockIdx.x * warps + (threadIdx.x >> 5); k < k_end; k += stride)
-    decode_block_fast(a, sh, k, mode);
+    decode_block_fast(a, k, mode);
 }
 
 template <int NT>

@@ -500,6 +500,12 @@ struct FastShared {
   __align__(16) uint32_t ring[kFastThreads * kRingStride];
 };
 
+// The fast decoders' shared state, one per CTA of any kernel that uses it.  The
+// block decoders below are separate (not inlined) functions, so that each gets
+// its own register allocation; they reach the tables through this symbol, not a
+// parameter, so that their accesses stay shared-memory loads.
+static __shared__ FastShared g_fast;
+
 // The lookup tables of T into shared memory (all threads of the CTA).
 static __device__ __forceinline__ void load_fast_tables(FastShared& sh, const DecTables* T,
                                                         int tid, int nt) {
@@ -785,7 +791,8 @@ __device__ __forceinline__ uint32_t ring_take(const FastShared& sh, RingWin& w, 
 }
 
 template <int kMode>
-__device__ void decode_block_warp(const DecodeArgs& a, FastShared& sh, uint32_t k) {
+__device__ __noinline__ void decode_block_warp(const DecodeArgs& a, uint32_t k) {
+  FastShared& sh = g_fast;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t W = sh.c.W;
   RecInfo r;
@@ -987,7 +994,8 @@ static __device__ __forceinline__ void skip_symbol0(const FastShared& sh, GWin& 
 }
 
 template <int K1, int K2, bool kRep>
-__device__ void decode_block_warp0(const DecodeArgs& a, FastShared& sh, uint32_t k) {
+__device__ __noinline__ void decode_block_warp0(const DecodeArgs& a, uint32_t k) {
+  FastShared& sh = g_fast;
   constexpr uint32_t kCap = K1 == 3 ? 10u : (uint32_t)kLutMaxBits;  // bits per counting step
   constexpr uint32_t kG1 = K1 == 3 ? 15u : 16u;                      // counting steps per refill
   const uint32_t lane = threadIdx.x & 31;
@@ -1165,14 +1173,14 @@ static __device__ __forceinline__ int fast_mode(const DecTables* T, const CanonT
   return c.maxlen <= 32 ? 1 : 2;
 }
 
-static __device__ __forceinline__ void decode_block_fast(const DecodeArgs& a, FastShared& sh,
+static __device__ __forceinline__ void decode_block_fast(const DecodeArgs& a,
                                                          uint32_t k, int mode) {
   if (mode == 0) {
-    if (sh.fill_k == 4) decode_block_warp0<3, 4, true>(a, sh, k);
-    else if (sh.fill_k == 3) decode_block_warp0<3, 3, true>(a, sh, k);
-    else decode_block_warp0<2, 2, false>(a, sh, k);
-  } else if (mode == 1) decode_block_warp<1>(a, sh, k);
-  else decode_block_warp<2>(a, sh, k);
+    if (g_fast.fill_k == 4) decode_block_warp0<3, 4, true>(a, k);
+    else if (g_fast.fill_k == 3) decode_block_warp0<3, 3, true>(a, k);
+    else decode_block_warp0<2, 2, false>(a, k);
+  } else if (mode == 1) decode_block_warp<1>(a, k);
+  else decode_block_warp<2>(a, k);
 }
 
 // ================================================================ generic kernel
