@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kScanThreads) encode_scan_kernel(EncodeArgs a)
   }
 }
 
-__global__ void __launch_bounds__(kEncThreads, 3) encode_pack_kernel(EncodeArgs a) {
+__global__ void __launch_bounds__(kEncThreads, 4) encode_pack_kernel(EncodeArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   PackShared& sh = *reinterpret_cast<PackShared*>(smem_raw);
   // size, capacity, time-out or code errors were found before packing
