@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kScanThreads) batch_scan_kernel(BatchCtl* ctl,
 }
 
 // ------------------------------------------------------------- packing
-__global__ void __launch_bounds__(kEncThreads, 4) batch_pack_kernel(BatchCtl* ctl,
+__global__ void __launch_bounds__(kEncThreads, 3) batch_pack_kernel(BatchCtl* ctl,
                                                                     const BatchComp* comps) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   PackShared& sh = *reinterpret_cast<PackShared*>(smem_raw);
