@@ -676,13 +676,15 @@ struct RingWin {
   }
 };
 
-// How the fast decoder reads codes: kMode 0 -- the code is complete and no
+// How the fast decoder reads codes.  Mode 0 -- the code is complete and no
 // code is longer than the table width W, so every table entry resolves at
-// least one symbol; kMode 1 -- codes of up to 32 bits: a longer code is
-// decoded from the window itself (filled before every step, so it holds more
-// than 32 bits), through the second-level table when there is one; kMode 2 --
-// any length: a longer code is read straight from memory and restarts the
-// window.
+// least one symbol: decode_block_warp0, with its own table layout.  The
+// general layout (lut_entry) serves decode_block_warp: kMode 1 -- codes of up
+// to 32 bits: a longer code is decoded from the window itself (filled before
+// every step, so it holds more than 32 bits), through the second-level table
+// when there is one; kMode 2 -- any length: a longer code is read straight
+// from memory and restarts the window.  (decode_block_warp's kMode 0 branches
+// serve no caller now.)
 
 // 64-bit window over the payload words read straight from global memory
 // (through L1), refilled one word at a time: the fix-up's short walks and

@@ -67,8 +67,11 @@ def _sample(lengths: np.ndarray, n: int, seed: int) -> np.ndarray:
 
 
 @pytest.mark.parametrize("name", sorted(CODES))
-@pytest.mark.parametrize("W", [12, 11, 10])
+@pytest.mark.parametrize("W", [12, 11, 10, 9, 8])
 def test_given_code_round_trip(hz, name, W):
+    """W >= 10 with codes of at most 10 bits: the replicated 10-bit table; W of 8
+    or 9 with codes that fit: the W-bit table of the same layout; longer codes
+    or incomplete codes: the general table with its second level."""
     lengths = CODES[name]
     codes = hz.make_codes(lengths, oracle.canonical_codes(lengths))
     ctx = hz.Context(0)
