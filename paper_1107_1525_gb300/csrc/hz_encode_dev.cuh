@@ -296,6 +296,7 @@ struct PackShared {
   uint32_t wsum[kEncThreads / 32];
   Summary warp_sum[kEncThreads / 32];
   uint32_t prev_bits;
+  __align__(16) uint8_t prev32[32];  // the 32 input bytes before the tile (single-record path)
   __align__(16) uint32_t stage[kEncStageWords + 4];
 };
 
@@ -329,6 +330,29 @@ __device__ uint32_t bits_before(const PackShared& sh, const uint8_t* in, uint32_
     --j;
   }
   return (uint32_t)(v & ((1u << r) - 1u));
+}
+
+// bits_before from the 32 bytes before the tile, staged in shared memory by a
+// cp.async that thread 0 issues when the tile starts (so that the input's
+// latency overlaps the tile's own loads): at most 31 codes make up r < 32 bits.
+template <bool kLong>
+__device__ uint32_t bits_before_staged(const PackShared& sh, uint32_t r) {
+  uint64_t v = 0;
+  uint32_t got = 0;
+  for (int j = 31; j >= 0 && got < r; --j) {
+    uint32_t l;
+    uint64_t c;
+    lookup<kLong>(sh, sh.prev32[j], l, c);
+    if (got < 64) v |= c << got;
+    got += l;
+  }
+  return (uint32_t)(v & ((1u << r) - 1u));
+}
+static __device__ __forceinline__ void stage_prev32(PackShared& sh, const uint8_t* src) {
+  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(sh.prev32);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16), "l"(src + 16) : "memory");
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
 // Pack one thread's 32 cached entries (code << 6 | len) MSB-first into
@@ -424,6 +448,10 @@ __device__ __noinline__ void pack_tile_single(PackShared& sh, uint32_t tile, con
   const ScanState S{a.tiles[tile].pre_O, a.tiles[tile].pre_b};
   const uint64_t O1 = g.starts_record ? S.O + 1 + ceil32(S.b) : S.O;
   const uint32_t b0 = g.starts_record ? 0u : S.b;
+  const uint32_t r_prev = b0 & 31u;  // bits of the previous tile in this tile's first word
+  const uint8_t* prev_src = a.in + g.lo - 32;
+  const bool staged = r_prev && g.lo >= 32 && (((uintptr_t)prev_src) & 15) == 0;
+  if (tid == 0 && staged) stage_prev32(sh, prev_src);
 
   uint32_t x[kEncSymPerThread / 4];
   load_symbols(a.in + g.g0, g.my_cnt, x);
@@ -462,12 +490,21 @@ __device__ __noinline__ void pack_tile_single(PackShared& sh, uint32_t tile, con
   const uint32_t nwords = ((bend - 1) >> 5) - (b0 >> 5) + 1;
   const uint32_t off = (uint32_t)((((uintptr_t)rec_words) >> 2) + W0) & 3u;
   if (total == 0 || off + nwords > (uint32_t)kEncStageWords + 4) {
-    if (tid == 0) set_error(a.st, HZ_ERR_ARG, 0x206);
+    if (tid == 0) {
+      set_error(a.st, HZ_ERR_ARG, 0x206);
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
     return;  // uniform
   }
-  const uint32_t r_prev = b0 & 31u;
   for (uint32_t i = tid; i < off + nwords; i += kEncThreads) sh.stage[i] = 0;
-  if (tid == 0 && r_prev) sh.prev_bits = bits_before<false>(sh, a.in, g.lo, r_prev);
+  if (tid == 0 && r_prev) {
+    if (staged) {
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      sh.prev_bits = bits_before_staged<false>(sh, r_prev);
+    } else {
+      sh.prev_bits = bits_before<false>(sh, a.in, g.lo, r_prev);
+    }
+  }
   __syncthreads();
   if (tid == 0 && r_prev) sh.stage[off] = sh.prev_bits << (32 - r_prev);
   __syncthreads();
