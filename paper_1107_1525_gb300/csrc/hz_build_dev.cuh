@@ -45,22 +45,33 @@ static __device__ void build_codes_device(DevState* st, int from_hist, const Len
       if (t == 0) s_len[leaf_sym[0]] = 1;  // a single distinct symbol: one 1-bit code
     } else if (m >= 2) {
       if (t == 0) {
+        // One thread, so every shared-memory latency on the loop's path would
+        // be paid in full: the heads of both queues and the element after
+        // each are kept in registers, and the loads run one element ahead.
         int li = 0, qh = 0, qt = 0;
+        uint32_t lhead = leaf_w[0], lnext = leaf_w[1];  // leaf_w[li], leaf_w[li + 1]
+        uint32_t ihead = 0, inext = 0;  // int_w[qh] if qh < qt, int_w[qh + 1] if qh + 1 < qt
         for (int k = 0; k < m - 1; ++k) {
           uint32_t w = 0;
 #pragma unroll
           for (int r = 0; r < 2; ++r) {
-            bool take_leaf = li < m && (qh >= qt || leaf_w[li] <= int_w[qh]);
+            const bool take_leaf = li < m && (qh >= qt || lhead <= ihead);
             if (take_leaf) {
-              w += leaf_w[li];
+              w += lhead;
               leaf_par[li] = k;
               ++li;
+              lhead = lnext;
+              lnext = li + 1 < m ? leaf_w[li + 1] : 0u;
             } else {
-              w += int_w[qh];
+              w += ihead;
               anc[0][qh] = k;
               ++qh;
+              ihead = inext;
+              inext = qh + 1 < qt ? int_w[qh + 1] : 0u;
             }
           }
+          if (qt == qh) ihead = w;           // the queue was empty
+          else if (qt == qh + 1) inext = w;  // it held one node
           int_w[qt++] = w;
         }
         anc[0][m - 2] = -1;  // the last merge is the root
