@@ -21,6 +21,7 @@ static __device__ void build_codes_device(DevState* st, int from_hist, const Len
   __shared__ uint32_t s_len[256];
   __shared__ uint32_t cnt[65];
   __shared__ uint64_t first[65];
+  __shared__ uint16_t s_wcnt[256 / 32][kMaxLen + 1];  // symbols of each length per warp
   __shared__ int s_ok;
   const int t = threadIdx.x;
 
@@ -100,6 +101,7 @@ static __device__ void build_codes_device(DevState* st, int from_hist, const Len
   }
   if (t < 65) cnt[t] = 0;
   if (t == 0) s_ok = 1;
+  for (int i = t; i < (256 / 32) * (kMaxLen + 1); i += 256) (&s_wcnt[0][0])[i] = 0;
   __syncthreads();
   const uint32_t myl = s_len[t];
   if (myl > (uint32_t)kMaxLen) s_ok = 0;
@@ -130,9 +132,16 @@ static __device__ void build_codes_device(DevState* st, int from_hist, const Len
     st->codes.maxlen = maxl;
     st->codes.nsym = nsym;
   }
+  // rank of t among the symbols of its length: its warp's lanes below it
+  // with that length, plus those of the earlier warps
+  const uint32_t lane = t & 31, warp = t >> 5;
+  const uint32_t peers = __match_any_sync(0xFFFFFFFFu, myl);
+  if (myl <= (uint32_t)kMaxLen && lane == (uint32_t)(__ffs(peers) - 1))
+    s_wcnt[warp][myl] = (uint16_t)__popc(peers);
   __syncthreads();
-  uint32_t rank = 0;
-  for (int u = 0; u < t; ++u) rank += s_len[u] == myl;
+  uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+  if (myl <= (uint32_t)kMaxLen)
+    for (uint32_t w = 0; w < warp; ++w) rank += s_wcnt[w][myl];
   const uint64_t mycode = (myl && myl <= (uint32_t)kMaxLen) ? first[myl] + rank : 0;
   st->codes.len[t] = (uint8_t)myl;
   st->codes.code[t] = mycode;

@@ -176,11 +176,22 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
     if (t == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x301);
     return;  // uniform
   }
-  // symbols in (length, byte) order
-  if (l) {
-    uint32_t rank = 0;
-    for (int u = 0; u < t; ++u) rank += s_len[u] == l;
-    s_sorted[offs[l] + rank] = (uint8_t)t;
+  // symbols in (length, byte) order: the rank among the symbols of the same
+  // length is the count of lower lanes of the warp with it plus the counts of
+  // the earlier warps
+  __shared__ uint16_t s_wcnt[256 / 32][kMaxLen + 1];
+  {
+    const uint32_t lane = t & 31, warp = t >> 5;
+    for (int i = t; i < (256 / 32) * (kMaxLen + 1); i += blockDim.x) (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, l);
+    if (lane == (uint32_t)(__ffs(peers) - 1)) s_wcnt[warp][l] = (uint16_t)__popc(peers);
+    __syncthreads();
+    if (l) {
+      uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+      for (uint32_t w = 0; w < warp; ++w) rank += s_wcnt[w][l];
+      s_sorted[offs[l] + rank] = (uint8_t)t;
+    }
   }
   __syncthreads();
   T->sorted[t] = s_sorted[t];
@@ -209,6 +220,7 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   __shared__ uint8_t s_ext[1 << kLutMaxBits];     // extra bits of an escape value, else 0
   __shared__ uint16_t s_base[1 << kLutMaxBits];   // its first second-level entry
   __shared__ uint32_t s_part[256];
+  __shared__ uint32_t s_wpart[256 / 32];
   __shared__ uint32_t s_l2_total;
   const uint32_t nv = 1u << W, per = (nv + blockDim.x - 1) / blockDim.x;
   uint32_t my_l2 = 0;
@@ -220,8 +232,7 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   uint32_t nshort = 0;
   for (int k = 1; k <= W && k <= (int)maxl; ++k) nshort += cnt[k];
   if ((uint32_t)t < nshort) {
-    uint32_t k = 1;
-    while (offs[k] + cnt[k] <= (uint32_t)t) ++k;  // the length of sorted code t
+    const uint32_t k = s_len[s_sorted[t]];  // the length of sorted code t
     s_lj[t] = (uint32_t)((first[k] + (t - offs[k])) << (W - k));
   }
   __syncthreads();
@@ -235,9 +246,8 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
         else hi_i = mid;
       }
       if (s_lj[lo_i] <= v) {
-        uint32_t k = 1;
-        while (offs[k] + cnt[k] <= lo_i) ++k;
-        if (v - s_lj[lo_i] < (1u << (W - k))) e1 = (uint16_t)(s_sorted[lo_i] | (k << 8));
+        const uint32_t sym = s_sorted[lo_i], k = s_len[sym];
+        if (v - s_lj[lo_i] < (1u << (W - k))) e1 = (uint16_t)(sym | (k << 8));
       }
     }
     s_t1[v] = e1;
@@ -297,16 +307,24 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
       T->lut[u] = lut0_entry(used, ns, l0, e1 & 0xFFu);
     }
   }
-  s_part[t] = my_l2;
-  __syncthreads();
-  if (t == 0) {
-    uint32_t acc = 0;
-    for (uint32_t i = 0; i < blockDim.x; ++i) {
-      const uint32_t c2 = s_part[i];
-      s_part[i] = acc;
-      acc += c2;
+  {
+    // exclusive scan of the threads' second-level sizes (value order)
+    const uint32_t lane = t & 31, warp = t >> 5;
+    uint32_t inc = my_l2;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+      if (lane >= (uint32_t)d) inc += o;
     }
-    s_l2_total = acc;
+    if (lane == 31) s_wpart[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+      before += w < warp ? s_wpart[w] : 0u;
+      total += s_wpart[w];
+    }
+    s_part[t] = before + inc - my_l2;
+    if (t == 0) s_l2_total = total;
   }
   __syncthreads();
   const uint32_t l2_total = s_l2_total;
