@@ -528,12 +528,10 @@ hz_status hz_decompress(hz_ctx* c, const uint8_t* d_in, uint64_t in_len, uint8_t
                 [&] { return launch_decode_chase(a, c->d_dec, c->cs, c->num_sms, s); });
     if (st != HZ_OK) return st;
   }
-  st = launch(c, K_DECODE, s, [&] {
+  // (blocks longer than 64 KiB are decoded by the same launch, a CTA per block)
+  return launch(c, K_DECODE, s, [&] {
     return launch_decode_blocks(a, c->d_dec, c->opt_dec_threads, c->num_sms, s);
   });
-  if (st != HZ_OK) return st;
-  return launch(c, K_DECODE_GENERIC, s,
-                [&] { return launch_decode_generic(a, c->d_dec, c->num_sms, s); });
 }
 
 // Decompress a large host-resident stream with an index as a pipeline of
@@ -617,11 +615,6 @@ static hz_status decompress_host_pipelined(hz_ctx* c, const uint8_t* h_in, uint6
             cudaSuccess)
       st = HZ_ERR_CUDA;
   }
-  a.k_begin = 0;
-  a.k_end = 0xFFFFFFFFu;
-  if (st == HZ_OK)
-    st = launch(c, K_DECODE_GENERIC, s,
-                [&] { return launch_decode_generic(a, c->d_dec, c->num_sms, s); });
   const bool in_done = cudaStreamSynchronize(c->s_in) == cudaSuccess;
   const bool out_done = cudaStreamSynchronize(c->s_out) == cudaSuccess;
   if (st != HZ_OK) {

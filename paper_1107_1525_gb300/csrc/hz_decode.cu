@@ -4,10 +4,10 @@
 //
 // decode_setup_kernel (one CTA) parses and checks the container header and
 // builds the canonical decode tables: per-length first code and count, the
-// symbols in (length, byte) order, and a 2^W-entry lookup table whose entry v
-// resolves the first one or two codes that prefix the W-bit value v.  For
+// symbols in (length, byte) order, and a lookup table indexed by the next W
+// (or 10) payload bits, in one of two layouts (hz_decode_dev.cuh).  For
 // streams without a stored index it rebuilds the offset table by walking the
-// delimiters (the paper's own scheme).
+// delimiters (the paper's own scheme), or leaves that to the chase kernel.
 //
 // The paper gives each block to one thread; a 64 KiB block is then a chain of
 // 65 536 dependent table lookups, far too long for a GPU.  Here a block's
@@ -24,12 +24,10 @@
 // decode_fast_kernel does this with one warp per block of at most 64 KiB:
 // lane i takes the i-th of 32 equal word ranges of the payload (about 2000
 // symbols each, so the resynchronisation costs next to nothing), the fix-up
-// and the scan are warp shuffles, the payload is read through L1 and each
-// lane writes its contiguous run of decoded bytes with 16-byte stores.  Only
-// the lookup table lives in shared memory, so about 40 warps share an SM and
-// hide each other's table and load latency.  decode_generic_kernel decodes
-// larger blocks with a whole CTA per block, straight from and to global
-// memory.
+// and the scan are warp shuffles, every lane reads its range through a
+// cp.async ring in shared memory and writes its contiguous run of decoded
+// bytes with 16-byte stores.  Larger blocks are decoded by the same launch,
+// one CTA per block.
 #include "hz_decode_dev.cuh"
 
 namespace hz {
@@ -40,11 +38,33 @@ __global__ void __launch_bounds__(256) decode_setup_kernel(DecodeArgs a, DecTabl
   decode_setup_device(a, T);
 }
 
+// Blocks longer than kFastMaxB: one CTA per block (decode_block_generic), its
+// shared state laid over the fast decoder's, so that no second launch is needed.
+struct GenAll {
+  GenShared sh;
+  GenBlockShared<kFastThreads> bs;
+};
+static_assert(sizeof(GenAll) <= sizeof(FastShared), "the generic state fits the fast one");
+
+__device__ __noinline__ void decode_generic_blocks(const DecodeArgs& a, const DecTables* T) {
+  GenAll& g = *reinterpret_cast<GenAll*>(&g_fast);
+  const int W = (int)T->lut_bits;
+  for (int i = threadIdx.x; i < (1 << W); i += kFastThreads) g.sh.lut[i] = T->lut[i];
+  load_canon(g.sh.c, T, threadIdx.x, kFastThreads);
+  __syncthreads();
+  const uint32_t k_end = a.k_end < g.sh.c.nb ? a.k_end : g.sh.c.nb;
+  for (uint32_t k = a.k_begin + blockIdx.x; k < k_end; k += gridDim.x)
+    decode_block_generic<kFastThreads>(a, g.sh, g.bs, k);
+}
+
 __global__ void __launch_bounds__(kFastThreads, 3) decode_fast_kernel(DecodeArgs a,
                                                                   const DecTables* T) {
   FastShared& sh = g_fast;
   if (!T->ok) return;
-  if (!fast_block_size(T->B)) return;  // every block goes to the generic kernel
+  if (!fast_block_size(T->B)) {  // uniform: every CTA takes whole blocks
+    decode_generic_blocks(a, T);
+    return;
+  }
   load_fast_tables(sh, T, threadIdx.x, kFastThreads);
   __syncthreads();
   const uint32_t warps = kFastThreads / 32;
@@ -53,19 +73,6 @@ __global__ void __launch_bounds__(kFastThreads, 3) decode_fast_kernel(DecodeArgs
   const uint32_t k_end = a.k_end < sh.c.nb ? a.k_end : sh.c.nb;
   for (uint32_t k = a.k_begin + blockIdx.x * warps + (threadIdx.x >> 5); k < k_end; k += stride)
     decode_block_fast(a, k, mode);
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT) decode_generic_kernel(DecodeArgs a, const DecTables* T) {
-  __shared__ GenShared sh;
-  __shared__ GenBlockShared<NT> bs;
-  // nothing to do unless some block was left to this kernel
-  if (!T->ok || a.st->dec_deferred == 0) return;
-  const int W = (int)T->lut_bits;
-  for (int i = threadIdx.x; i < (1 << W); i += NT) sh.lut[i] = T->lut[i];
-  load_canon(sh.c, T, threadIdx.x, NT);
-  __syncthreads();
-  for (uint32_t k = blockIdx.x; k < sh.c.nb; k += gridDim.x) decode_block_generic<NT>(a, sh, bs, k);
 }
 
 // ================================================================ launchers
@@ -89,15 +96,6 @@ cudaError_t launch_decode_blocks(const DecodeArgs& a, const DecTables* T, int th
     if (need < grid) grid = need ? need : 1;
   }
   decode_fast_kernel<<<(unsigned)grid, kFastThreads, 0, s>>>(a, T);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_decode_generic(const DecodeArgs& a, const DecTables* T, int num_sms,
-                                  cudaStream_t s) {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_generic_kernel<256>, 256, 0);
-  if (per_sm < 1) per_sm = 1;
-  decode_generic_kernel<256><<<num_sms * per_sm, 256, 0, s>>>(a, T);
   return cudaGetLastError();
 }
 

@@ -57,7 +57,7 @@ constexpr int kMaxScanCtas = (int)((1ull << 32) / kEncTile / kScanTilesPerCta); 
 struct DevState {
   uint32_t error;           // first error recorded (as -hz_status), 0 = none
   uint32_t error_where;     // kernel-specific detail for debugging
-  uint32_t dec_deferred;    // blocks the fast decode kernel left to the generic one
+  uint32_t dec_deferred;    // blocks decoded one CTA per block (blocks over 64 KiB)
   uint32_t pad0;
   // ---- cleared before every compress (one memset from here to `codes`)
   uint32_t tile_counter;    // ticket of the scan CTAs
@@ -179,7 +179,4 @@ size_t dec_tables_bytes();
 cudaError_t launch_decode_setup(const DecodeArgs& a, DecTables* T, cudaStream_t s);
 cudaError_t launch_decode_blocks(const DecodeArgs& a, const DecTables* T, int threads, int num_sms,
                                  cudaStream_t s);
-cudaError_t launch_decode_generic(const DecodeArgs& a, const DecTables* T, int num_sms,
-                                  cudaStream_t s);
-
 }  // namespace hz

@@ -101,7 +101,8 @@ def test_build_codes_matches_oracle(hz, ctx):
 @pytest.mark.parametrize("n,B", [(1, 1), (1, 4096), (2, 1), (3, 3), (31, 1), (100, 7),
                                  (8191, 4096), (8192, 8192), (8193, 8192), (20_000, 1),
                                  (50_001, 33), (100_000, 100_000), (100_000, 1 << 24),
-                                 (262_147, 65_536), (300_000, 8191)])
+                                 (262_147, 65_536), (300_000, 8191), (600_000, 131_072),
+                                 (1_000_000, 262_144)])
 def test_sizes_and_block_sizes(hz, ctx, n, B):
     _check_round_trip(hz, ctx, _zipf(n, 1.1, n ^ B), B)
 
