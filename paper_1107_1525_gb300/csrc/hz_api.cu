@@ -45,7 +45,7 @@ struct hz_ctx {
   uint8_t* d_hout = nullptr;
   uint64_t d_hout_cap = 0;
   uint64_t* d_len = nullptr;
-  uint64_t* h_len = nullptr;
+  uint64_t* h_len = nullptr;  // [0]: a stream length; [1..]: the host pipeline's boundaries
   // streams without an index: the setup kernel sets *h_seen (mapped pinned
   // memory) when it meets one; from then on large streams get the parallel
   // chase and its scratch
@@ -161,7 +161,8 @@ hz_status hz_create(hz_ctx** out, int device, uint64_t mem_budget_bytes) {
             cudaMalloc(&c->d_len, sizeof(uint64_t)) == cudaSuccess &&
             cudaHostAlloc(&c->h_err, 4 * sizeof(uint32_t), cudaHostAllocDefault) == cudaSuccess &&
             cudaHostAlloc(&c->h_codes, sizeof(hz_codes), cudaHostAllocDefault) == cudaSuccess &&
-            cudaHostAlloc(&c->h_len, sizeof(uint64_t), cudaHostAllocDefault) == cudaSuccess;
+            cudaHostAlloc(&c->h_len, (kPipeGroups + 1) * sizeof(uint64_t),
+                          cudaHostAllocDefault) == cudaSuccess;
   if (ok) ok = cudaMemset(c->d_state, 0, sizeof(DevState)) == cudaSuccess;
   if (ok) {
     // streams without a stored index need a rebuilt offset table
@@ -409,19 +410,11 @@ hz_status hz_build_codes(hz_ctx* c, const uint8_t* d_in, uint64_t n, hz_codes* c
   return HZ_OK;
 }
 
-hz_status hz_compress(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32_t block_size,
-                      const hz_codes* codes, uint8_t* d_out, uint64_t out_cap,
-                      uint64_t* d_out_len, void* stream) {
-  if (!c || !d_out || !d_out_len || n > 0xFFFFFFFFull || (n && !d_in)) return HZ_ERR_ARG;
-  if (((uintptr_t)d_out & 3) || ((uintptr_t)d_out_len & 7)) return HZ_ERR_ARG;
-  if (block_size > kMaxBlock) return HZ_ERR_ARG;
-  if (codes && !codes_valid(codes)) return HZ_ERR_ARG;
-  DeviceGuard g(c->device);
-  cudaStream_t s = (cudaStream_t)stream;
-  const uint32_t B = block_size ? block_size : autotuned_block(c, n);
-  const uint64_t nb64 = (n + B - 1) / B;
-  const uint32_t nb = (uint32_t)nb64;
-  const uint32_t flags = c->opt_index ? kFlagIndex : 0;
+// The encoder's launch arguments for n bytes in blocks of B, and its per-tile
+// scratch (shared by hz_compress and the host-buffer pipeline).
+static hz_status encode_setup(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32_t B,
+                              uint8_t* d_out, uint64_t out_cap, uint64_t* d_out_len,
+                              EncodeArgs* a) {
   const uint32_t ntiles = (uint32_t)((n + kEncTile - 1) / kEncTile);
   if (ntiles > c->tiles_cap) {
     uint64_t cap = c->tiles_cap ? c->tiles_cap : 1024;
@@ -435,21 +428,38 @@ hz_status hz_compress(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32_t block
     }
     c->tiles_cap = (uint32_t)cap;
   }
-  hz_status st = enqueue_codes(c, d_in, n, codes, B, nb, flags, d_out, out_cap, d_out_len, s);
-  if (st != HZ_OK || n == 0) return st;
+  a->in = d_in;
+  a->n = n;
+  a->B = B;
+  a->nb = (uint32_t)((n + B - 1) / B);
+  a->flags = c->opt_index ? kFlagIndex : 0;
+  a->out = d_out;
+  a->out_cap = out_cap;
+  a->out_len = d_out_len;
+  a->st = c->d_state;
+  a->tiles = c->d_tiles;
+  a->ntiles = ntiles;
+  a->fdB = make_fastdiv(B);
+  a->tile_begin = 0;
+  a->tile_end = ntiles;
+  return HZ_OK;
+}
+
+hz_status hz_compress(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32_t block_size,
+                      const hz_codes* codes, uint8_t* d_out, uint64_t out_cap,
+                      uint64_t* d_out_len, void* stream) {
+  if (!c || !d_out || !d_out_len || n > 0xFFFFFFFFull || (n && !d_in)) return HZ_ERR_ARG;
+  if (((uintptr_t)d_out & 3) || ((uintptr_t)d_out_len & 7)) return HZ_ERR_ARG;
+  if (block_size > kMaxBlock) return HZ_ERR_ARG;
+  if (codes && !codes_valid(codes)) return HZ_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t B = block_size ? block_size : autotuned_block(c, n);
   EncodeArgs a;
-  a.in = d_in;
-  a.n = n;
-  a.B = B;
-  a.nb = nb;
-  a.flags = flags;
-  a.out = d_out;
-  a.out_cap = out_cap;
-  a.out_len = d_out_len;
-  a.st = c->d_state;
-  a.tiles = c->d_tiles;
-  a.ntiles = ntiles;
-  a.fdB = make_fastdiv(B);
+  hz_status st = encode_setup(c, d_in, n, B, d_out, out_cap, d_out_len, &a);
+  if (st != HZ_OK) return st;
+  st = enqueue_codes(c, d_in, n, codes, B, a.nb, a.flags, d_out, out_cap, d_out_len, s);
+  if (st != HZ_OK || n == 0) return st;
   st = launch(c, K_ENC_SUMMARY, s, [&] { return launch_encode_summary(a, c->num_sms, s); });
   if (st == HZ_OK) st = launch(c, K_ENC_SCAN, s, [&] { return launch_encode_scan(a, s); });
   if (st == HZ_OK) st = launch(c, K_ENC_PACK, s, [&] { return launch_encode_pack(a, c->num_sms, s); });
@@ -629,14 +639,117 @@ static hz_status decompress_host_pipelined(hz_ctx* c, const uint8_t* h_in, uint6
   return st;
 }
 
+// Compress a large host-resident buffer with the copies overlapped:
+//   - the input goes in as kPipeGroups chunks on s_in, and each chunk's
+//     histogram runs as soon as it has landed;
+//   - after code construction, the length-summing pass and the scan, one sync
+//     brings back the stream size and the start states of kPipeGroups - 1
+//     tile boundaries;
+//   - the tiles are then packed in kPipeGroups groups, and after each group
+//     the stream words it finished are copied out on s_out: every word before
+//     the delimiter of the record that is open where the next group starts
+//     (each record's words and delimiter come from its own tiles);
+//   - the header and the index (whose entries the packing writes) go last.
+// HZ_PENDING: the buffer is too small for the pipeline to pay.
+static hz_status compress_host_pipelined(hz_ctx* c, const uint8_t* h_in, uint64_t n,
+                                         uint32_t block_size, uint8_t* h_out, uint64_t out_cap,
+                                         uint64_t* out_len, cudaStream_t s) {
+  if (n < kPipeMinBytes || !c->s_in || !c->s_out) return HZ_PENDING;
+  const uint32_t B = block_size ? block_size : autotuned_block(c, n);
+  const uint64_t bound = hz_compress_bound(n, B);
+  const uint64_t dcap = out_cap < bound ? out_cap : bound;
+  hz_status st = grow((void**)&c->d_hin, &c->d_hin_cap, n);
+  if (st == HZ_OK) st = grow((void**)&c->d_hout, &c->d_hout_cap, dcap ? dcap : 16);
+  EncodeArgs a;
+  if (st == HZ_OK) st = encode_setup(c, c->d_hin, n, B, c->d_hout, dcap, c->d_len, &a);
+  if (st != HZ_OK) return st;
+  if (cudaMemsetAsync(&c->d_state->tile_counter, 0,
+                      offsetof(DevState, codes) - offsetof(DevState, tile_counter), s) !=
+      cudaSuccess)
+    return HZ_ERR_CUDA;
+  // input chunks of whole MiB (16-byte aligned for the histogram's loads)
+  const uint64_t chunk = ((n + kPipeGroups - 1) / kPipeGroups + (1u << 20) - 1) & ~((1ull << 20) - 1);
+  for (int gi = 0; gi < kPipeGroups && st == HZ_OK; ++gi) {
+    const uint64_t off = (uint64_t)gi * chunk;
+    if (off >= n) break;
+    const uint64_t len = n - off < chunk ? n - off : chunk;
+    if (cudaMemcpyAsync(c->d_hin + off, h_in + off, len, cudaMemcpyHostToDevice, c->s_in) !=
+            cudaSuccess ||
+        cudaEventRecord(c->e_in[gi], c->s_in) != cudaSuccess ||
+        cudaStreamWaitEvent(s, c->e_in[gi], 0) != cudaSuccess)
+      st = HZ_ERR_CUDA;
+    if (st == HZ_OK)
+      st = launch(c, K_HIST, s,
+                  [&] { return launch_histogram(c->d_hin + off, len, c->d_state, c->num_sms, s); });
+  }
+  LenParam none;
+  memset(&none, 0, sizeof(none));
+  if (st == HZ_OK)
+    st = launch(c, K_BUILD, s, [&] {
+      return launch_build_codes(c->d_state, 1, none, n, B, a.nb, a.flags, c->d_hout, dcap,
+                                c->d_len, s);
+    });
+  if (st == HZ_OK)
+    st = launch(c, K_ENC_SUMMARY, s, [&] { return launch_encode_summary(a, c->num_sms, s); });
+  if (st == HZ_OK) st = launch(c, K_ENC_SCAN, s, [&] { return launch_encode_scan(a, s); });
+  // tile groups, and the start state (open record's delimiter word) of each
+  uint32_t tg[kPipeGroups + 1];
+  for (int gi = 0; gi <= kPipeGroups; ++gi)
+    tg[gi] = (uint32_t)((uint64_t)a.ntiles * gi / kPipeGroups);
+  for (int gi = 1; gi < kPipeGroups && st == HZ_OK; ++gi)
+    if (cudaMemcpyAsync(c->h_len + gi, &a.tiles[tg[gi]].pre_O, 8, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+      st = HZ_ERR_CUDA;
+  if (st == HZ_OK && cudaMemcpyAsync(c->h_len, c->d_len, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    st = HZ_ERR_CUDA;
+  if (st != HZ_OK) {
+    cudaStreamSynchronize(c->s_in);
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  st = hz_sync(c, s);  // size, capacity and code errors are known here
+  *out_len = *c->h_len;
+  if (st != HZ_OK) return st;
+  if (*out_len > out_cap) return HZ_ERR_CAPACITY;
+  const uint64_t rec_base = kHeaderBytes + ((a.flags & kFlagIndex) ? 4ull * a.nb : 0ull);
+  uint64_t wb[kPipeGroups + 1];
+  wb[0] = 0;
+  for (int gi = 1; gi < kPipeGroups; ++gi) wb[gi] = c->h_len[gi];
+  wb[kPipeGroups] = (*out_len - rec_base) / 4;
+  for (int gi = 0; gi < kPipeGroups && st == HZ_OK; ++gi) {
+    a.tile_begin = tg[gi];
+    a.tile_end = tg[gi + 1];
+    st = launch(c, K_ENC_PACK, s, [&] { return launch_encode_pack(a, c->num_sms, s); });
+    if (st == HZ_OK && (cudaEventRecord(c->e_dec[gi], s) != cudaSuccess ||
+                        cudaStreamWaitEvent(c->s_out, c->e_dec[gi], 0) != cudaSuccess))
+      st = HZ_ERR_CUDA;
+    const uint64_t b0 = rec_base + 4 * wb[gi], b1 = rec_base + 4 * wb[gi + 1];
+    if (st == HZ_OK && b1 > b0 &&
+        cudaMemcpyAsync(h_out + b0, c->d_hout + b0, b1 - b0, cudaMemcpyDeviceToHost, c->s_out) !=
+            cudaSuccess)
+      st = HZ_ERR_CUDA;
+  }
+  if (st == HZ_OK &&
+      cudaMemcpyAsync(h_out, c->d_hout, rec_base, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess)
+    st = HZ_ERR_CUDA;
+  const bool out_done = cudaStreamSynchronize(c->s_out) == cudaSuccess;
+  const hz_status st2 = hz_sync(c, s);  // errors of the packing
+  if (st != HZ_OK) return st;
+  if (!out_done) return HZ_ERR_CUDA;
+  return st2;
+}
+
 hz_status hz_compress_host(hz_ctx* c, const uint8_t* h_in, uint64_t n, uint32_t block_size,
                            uint8_t* h_out, uint64_t out_cap, uint64_t* out_len, void* stream) {
   if (!c || !h_out || !out_len || (n && !h_in) || n > 0xFFFFFFFFull) return HZ_ERR_ARG;
+  if (block_size > kMaxBlock) return HZ_ERR_ARG;
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
+  hz_status st = compress_host_pipelined(c, h_in, n, block_size, h_out, out_cap, out_len, s);
+  if (st != HZ_PENDING) return st;
   const uint64_t bound = hz_compress_bound(n, block_size ? block_size : 1);
   const uint64_t dcap = out_cap < bound ? out_cap : bound;
-  hz_status st = grow((void**)&c->d_hin, &c->d_hin_cap, n ? n : 16);
+  st = grow((void**)&c->d_hin, &c->d_hin_cap, n ? n : 16);
   if (st == HZ_OK) st = grow((void**)&c->d_hout, &c->d_hout_cap, dcap ? dcap : 16);
   if (st != HZ_OK) return st;
   if (n && cudaMemcpyAsync(c->d_hin, h_in, n, cudaMemcpyHostToDevice, s) != cudaSuccess)

@@ -73,6 +73,8 @@ __device__ __forceinline__ EncodeArgs comp_args(const BatchComp& c) {
   a.tiles = c.tiles;
   a.ntiles = c.ntiles;
   a.fdB = c.fdB;
+  a.tile_begin = 0;
+  a.tile_end = c.ntiles;
   return a;
 }
 

@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(kEncThreads, 4) encode_pack_kernel(EncodeArgs 
   const uint32_t maxlen = a.st->codes.maxlen;
   pack_load_tables(sh, a);
   __syncthreads();
-  for (uint32_t i = blockIdx.x; i < a.ntiles; i += gridDim.x) {
+  for (uint32_t i = blockIdx.x; i < a.tile_end - a.tile_begin; i += gridDim.x) {
     // last tiles first: their input is still in L2 from the length-summing pass
-    pack_one_tile(sh, a.ntiles - 1 - i, maxlen);
+    pack_one_tile(sh, a.tile_end - 1 - i, maxlen);
     __syncthreads();
   }
 }
@@ -221,7 +221,9 @@ cudaError_t launch_encode_pack(const EncodeArgs& a, int num_sms, cudaStream_t s)
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_pack_kernel, kEncThreads, smem);
   const uint64_t grid = (uint64_t)num_sms * (per_sm > 0 ? per_sm : 1);
-  encode_pack_kernel<<<(unsigned)(grid < a.ntiles ? grid : a.ntiles), kEncThreads, smem, s>>>(a);
+  const uint32_t nt = a.tile_end - a.tile_begin;
+  if (nt == 0) return cudaSuccess;
+  encode_pack_kernel<<<(unsigned)(grid < nt ? grid : nt), kEncThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -142,6 +142,7 @@ struct EncodeArgs {
   TileStatus* tiles;
   uint32_t ntiles;
   FastDiv fdB;              // division by B
+  uint32_t tile_begin, tile_end;  // tiles the single-buffer packing launch packs
 };
 
 struct DecodeArgs {

@@ -98,6 +98,8 @@ extern "C" hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32
     a.st = st;
     a.tiles = tiles;
     a.ntiles = ntiles;
+    a.tile_begin = 0;
+    a.tile_end = ntiles;
     a.fdB = make_fastdiv(B);
     if (launch_encode_summary(a, num_sms, s) != cudaSuccess ||
         launch_encode_scan(a, s) != cudaSuccess || launch_encode_pack(a, num_sms, s) != cudaSuccess)

@@ -100,3 +100,18 @@ def test_host_decompress_capacity(hz):
     st, _ = hz.hz_decompress_host(ctx, _pinned(s), s.numel(), h_y, x.numel() - 1)
     assert st == hz.HZ_ERR_CAPACITY
     ctx.close()
+
+
+def test_pipelined_host_compress_capacity(hz):
+    """The pipelined host compression (inputs of 32 MiB and more) checks the
+    stream size against the caller's capacity before copying anything out."""
+    ctx = hz.Context(0)
+    x = datagen.mixed_buffer(n=40 * MiB, segment=8 * MiB, seed=6, device="cuda:0")
+    exact = hz.compress(x, 65536, ctx=ctx).cpu()
+    h_in = _pinned(x)
+    h_s = torch.empty(exact.numel(), dtype=torch.uint8, pin_memory=True)
+    st, _ = hz.hz_compress_host(ctx, h_in, x.numel(), 65536, h_s, exact.numel() - 1)
+    assert st == hz.HZ_ERR_CAPACITY
+    st, slen = hz.hz_compress_host(ctx, h_in, x.numel(), 65536, h_s, exact.numel())
+    assert st == 0 and slen == exact.numel() and torch.equal(h_s, exact)
+    ctx.close()
