@@ -498,11 +498,13 @@ __device__ __noinline__ void pack_tile_single(PackShared& sh, uint32_t tile, con
   }
   for (uint32_t i = tid; i < off + nwords; i += kEncThreads) sh.stage[i] = 0;
   if (tid == 0 && r_prev) {
+    // (codes of more than 26 bits: the entry table truncates them, so the
+    // length and code tables)
     if (staged) {
       asm volatile("cp.async.wait_all;\n" ::: "memory");
-      sh.prev_bits = bits_before_staged<false>(sh, r_prev);
+      sh.prev_bits = bits_before_staged<kKind == 2>(sh, r_prev);
     } else {
-      sh.prev_bits = bits_before<false>(sh, a.in, g.lo, r_prev);
+      sh.prev_bits = bits_before<kKind == 2>(sh, a.in, g.lo, r_prev);
     }
   }
   __syncthreads();

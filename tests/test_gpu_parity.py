@@ -156,6 +156,22 @@ def test_given_codes_beyond_26_and_32_bits(hz, ctx, maxlen):
     _check_round_trip(hz, ctx, x, 7, lengths=lens)
 
 
+def test_tile_start_inside_a_code_longer_than_26_bits(hz, ctx):
+    """A tile that starts 29 bits into a word whose first bits belong to a
+    30-bit code of the tile before: the packer rebuilds those bits from the
+    previous tile's input, and codes of more than 26 bits must come from its
+    full code table (its packed entry table keeps only 26).  One 27-bit code,
+    then 30-bit codes: 27 + 8191 * 30 = 29 (mod 32) bits end tile 0."""
+    maxlen = 30
+    lens = np.zeros(256, dtype=np.uint8)
+    lens[:maxlen] = np.arange(1, maxlen + 1)
+    lens[maxlen] = maxlen  # the chain 1, 2, ..., 30, 30 is complete
+    x = np.full(4 * 8192 + 100, maxlen - 1, dtype=np.uint8)  # symbol 29: 30 bits
+    x[0] = 26  # symbol 26: 27 bits
+    for B in (8192, 16384):
+        _check_round_trip(hz, ctx, x, B, lengths=lens)
+
+
 def test_no_index_mode(hz, ctx):
     x = _zipf(500_000, 1.2, 9)
     _check_round_trip(hz, ctx, x, 4096, index=False)
