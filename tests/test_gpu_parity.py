@@ -102,7 +102,7 @@ def test_build_codes_matches_oracle(hz, ctx):
                                  (8191, 4096), (8192, 8192), (8193, 8192), (20_000, 1),
                                  (50_001, 33), (100_000, 100_000), (100_000, 1 << 24),
                                  (262_147, 65_536), (300_000, 8191), (600_000, 131_072),
-                                 (1_000_000, 262_144)])
+                                 (1_000_000, 262_144), (196_608, 65_536), (196_611, 65_537)])
 def test_sizes_and_block_sizes(hz, ctx, n, B):
     _check_round_trip(hz, ctx, _zipf(n, 1.1, n ^ B), B)
 
@@ -142,7 +142,7 @@ def test_fibonacci_frequencies_long_codes(hz, ctx):
     assert max(format_reader.read_container(s.tobytes())["lengths"]) >= 28
 
 
-@pytest.mark.parametrize("maxlen", [27, 33, 47, 64])
+@pytest.mark.parametrize("maxlen", [26, 27, 31, 32, 33, 47, 64])
 def test_given_codes_beyond_26_and_32_bits(hz, ctx, maxlen):
     # the Kraft-complete chain 1, 2, ..., maxlen, maxlen exercises the long-code paths
     lens = np.zeros(256, dtype=np.uint8)
