@@ -114,3 +114,19 @@ def test_corrupt_record_is_reported(hz, name):
         assert st == hz.HZ_ERR_CORRUPT
     assert torch.equal(hz.decompress(s, ctx=ctx).cpu(), torch.from_numpy(x))
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["chain10", "chain8", "chain12", "chain14"])
+@pytest.mark.parametrize("B", [1, 7, 33, 1000])
+def test_small_blocks(hz, name, B):
+    """Blocks of a few symbols: fewer bit ranges than lanes, ranges shorter than
+    one refill period, records of one or two words."""
+    lengths = CODES[name]
+    codes = hz.make_codes(lengths, oracle.canonical_codes(lengths))
+    ctx = hz.Context(0)
+    x = _sample(lengths, 20_000 + B, 7 + B)
+    xd = torch.from_numpy(x).to(DEV)
+    s = hz.compress(xd, B, ctx=ctx, codes=codes)
+    assert np.array_equal(s.cpu().numpy(), oracle.compress(x, B, lengths=lengths))
+    assert torch.equal(hz.decompress(s, ctx=ctx), xd)
+    ctx.close()

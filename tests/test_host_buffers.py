@@ -115,3 +115,21 @@ def test_pipelined_host_compress_capacity(hz):
     st, slen = hz.hz_compress_host(ctx, h_in, x.numel(), 65536, h_s, exact.numel())
     assert st == 0 and slen == exact.numel() and torch.equal(h_s, exact)
     ctx.close()
+
+
+@pytest.mark.parametrize("B", [4096, 10000, 65536])
+def test_pipelined_host_compress_ragged(hz, B):
+    """The pipelined host compression on a size that is no multiple of the
+    input chunks or the tiles, with blocks whose tiles hold record starts
+    (4096: the chunked packer; 10000: the general one): its stream equals the
+    device-buffer path's and the oracle's."""
+    ctx = hz.Context(0)
+    n = 33 * MiB + 12345
+    x = datagen.mixed_buffer(n=n, segment=4 * MiB, seed=11, device="cuda:0")
+    st, s, y, h_in = _host_round_trip(hz, ctx, x, B)
+    assert st == 0 and torch.equal(y, h_in)
+    assert torch.equal(hz.compress(x, B, ctx=ctx).cpu(), s)
+    xs = x[: 3 * MiB].cpu().numpy()  # and the oracle agrees with the device path
+    assert np.array_equal(hz.compress(x[: 3 * MiB], B, ctx=ctx).cpu().numpy(),
+                          oracle.compress(xs, B))
+    ctx.close()
