@@ -258,10 +258,15 @@ typedef struct {
  * budget and HZ_OPT_BATCH_MAX_REQS (continuous batching).  HZ_ERR_BUSY if the
  * submission alone exceeds the budget; HZ_ERR_ARG for a malformed request
  * (unknown op, NULL pointer, src_len >= 2^32, block_size > 2^24, d_dst not
- * 4-byte aligned, or a decompress d_src not 4-byte aligned).  The caller keeps
- * every buffer alive and untouched until the ticket completes.
+ * 4-byte aligned, or a decompress d_src not 4-byte aligned).  The batch that
+ * carries the submission runs on the context's own streams, after the work
+ * enqueued on `stream` (NULL = the legacy default stream) before this call:
+ * the caller may write the sources there and submit without waiting.  The
+ * caller keeps every buffer alive and untouched until the ticket completes.
+ * HZ_ERR_CUDA if the ordering event cannot be recorded on `stream`.
  */
-hz_status hz_submit(hz_ctx* ctx, const hz_request* reqs, uint32_t count, uint64_t* ticket_out);
+hz_status hz_submit(hz_ctx* ctx, const hz_request* reqs, uint32_t count, uint64_t* ticket_out,
+                    void* stream);
 
 /*
  * Wait up to timeout_ns (0 = just look, < 0 = forever) for batch `ticket`.
@@ -280,7 +285,9 @@ hz_status hz_poll(hz_ctx* ctx, uint64_t ticket, int64_t timeout_ns, hz_status* p
  * when a slot frees up (see hz_submit).  An item whose req.d_dst is NULL
  * takes req.dst_cap bytes of the device ring d_ring[0..ring_bytes) (256-byte
  * aligned, owned by the caller) from submission to completion, and waits for
- * room when the ring is full.  Blocks until every item has completed; then
+ * room when the ring is full.  The call first waits for all work on the
+ * device (so the sources are ready whichever stream wrote them), then starts
+ * its clock.  Blocks until every item has completed; then
  * records[i] (host array of `count`) holds its times (seconds from the
  * start: handed to the batcher, completion seen on the host), status, result
  * length, the device batch that carried it and its ring offset (~0 for items

@@ -794,10 +794,11 @@ hz_status hz_decompress_host(hz_ctx* c, const uint8_t* h_in, uint64_t in_len, ui
   return cudaStreamSynchronize(s) == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;
 }
 
-hz_status hz_submit(hz_ctx* c, const hz_request* reqs, uint32_t count, uint64_t* ticket_out) {
+hz_status hz_submit(hz_ctx* c, const hz_request* reqs, uint32_t count, uint64_t* ticket_out,
+                    void* stream) {
   if (!c || !ticket_out || (count && !reqs)) return HZ_ERR_ARG;
   DeviceGuard g(c->device);
-  return hz_batch_submit(c->batch, c, reqs, count, ticket_out);
+  return hz_batch_submit(c->batch, c, reqs, count, ticket_out, true, stream);
 }
 
 hz_status hz_poll(hz_ctx* c, uint64_t ticket, int64_t timeout_ns, hz_status* per_req,

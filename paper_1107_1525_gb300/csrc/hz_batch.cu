@@ -48,6 +48,10 @@ struct Job {
   // plain mode: the job's records in the plain ring, and its completion event
   uint32_t plain_pos = 0;
   cudaEvent_t plain_done = nullptr;
+  // recorded at submission on the caller's stream: the launch that carries
+  // the job waits for it, so work the caller enqueued before hz_submit (that
+  // writes the sources, or reads the destinations) comes first
+  cudaEvent_t ready = nullptr;
 };
 
 struct Slot {
@@ -112,7 +116,19 @@ struct BatchState {
   uint64_t* h_plain_lens = nullptr;
   uint32_t plain_head = 0;      // next free record
   uint32_t plain_inflight = 0;  // records held by unfinished plain jobs
+  std::vector<cudaEvent_t> free_events;  // for Job::ready
 };
+
+// Make `s` wait for the job's submission event and return the event to the
+// pool (a wait takes the event's state when it is enqueued, so the event can
+// be recorded again at once).
+static bool wait_ready(BatchState* b, Job* j, cudaStream_t s) {
+  if (!j->ready) return true;
+  const bool ok = cudaStreamWaitEvent(s, j->ready, 0) == cudaSuccess;
+  b->free_events.push_back(j->ready);
+  j->ready = nullptr;
+  return ok;
+}
 
 extern "C" hz_status hz_compress(hz_ctx*, const uint8_t*, uint64_t, uint32_t, const hz_codes*,
                                  uint8_t*, uint64_t, uint64_t*, void*);
@@ -233,8 +249,9 @@ BatchState* hz_batch_create(int device, int num_sms, uint64_t mem_budget) {
   return b;
 }
 
-static void free_job(Job* j) {
+static void free_job(BatchState* b, Job* j) {
   if (j->plain_done) cudaEventDestroy(j->plain_done);
+  if (j->ready) b->free_events.push_back(j->ready);
   delete j;
 }
 
@@ -252,7 +269,8 @@ void hz_batch_destroy(BatchState* b) {
   cudaFree(b->d_plain_lens);
   cudaFreeHost(b->h_plain_status);
   cudaFreeHost(b->h_plain_lens);
-  for (auto& kv : b->jobs) free_job(kv.second);
+  for (auto& kv : b->jobs) free_job(b, kv.second);
+  for (cudaEvent_t e : b->free_events) cudaEventDestroy(e);
   delete b;
 }
 
@@ -312,6 +330,10 @@ static hz_status launch_plain(BatchState* b, Job* j) {
   int32_t* d_status = b->d_plain_status + j->plain_pos;
   uint64_t* d_lens = b->d_plain_lens + j->plain_pos;
   if (cudaEventCreateWithFlags(&j->plain_done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return HZ_ERR_CUDA;
+  }
+  if (!wait_ready(b, j, b->plain_stream)) {
     cudaGetLastError();
     return HZ_ERR_CUDA;
   }
@@ -418,7 +440,9 @@ static hz_status launch_batched(BatchState* b, const std::vector<Job*>& group, i
   ctl.tile_base = s.d_bases + s.req_cap;
   ctl.unit_base = s.d_bases + 2ull * s.req_cap;
   *s.h_ctl = ctl;
-  if (cudaGraphLaunch(s.graph, s.stream) != cudaSuccess ||
+  bool waited = true;
+  for (Job* j : group) waited &= wait_ready(b, j, s.stream);
+  if (!waited || cudaGraphLaunch(s.graph, s.stream) != cudaSuccess ||
       cudaEventRecord(s.done, s.stream) != cudaSuccess) {
     cudaGetLastError();
     return HZ_ERR_CUDA;
@@ -569,7 +593,7 @@ static void progress(BatchState* b) {
 }
 
 hz_status hz_batch_submit(BatchState* b, hz_ctx* ctx, const hz_request* reqs, uint32_t count,
-                          uint64_t* ticket) {
+                          uint64_t* ticket, bool ordered, void* after) {
   b->ctx = ctx;
   uint64_t fp = 0;
   for (uint32_t i = 0; i < count; ++i) {
@@ -588,6 +612,22 @@ hz_status hz_batch_submit(BatchState* b, hz_ctx* ctx, const hz_request* reqs, ui
   if (b->budget && j->footprint > b->budget) {
     delete j;
     return HZ_ERR_BUSY;
+  }
+  if (ordered) {
+    if (!b->free_events.empty()) {
+      j->ready = b->free_events.back();
+      b->free_events.pop_back();
+    } else if (cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      j->ready = nullptr;
+      free_job(b, j);
+      return HZ_ERR_CUDA;
+    }
+    if (cudaEventRecord(j->ready, (cudaStream_t)after) != cudaSuccess) {
+      cudaGetLastError();
+      free_job(b, j);
+      return HZ_ERR_CUDA;
+    }
   }
   j->ticket = b->next_ticket++;
   b->queue.push_back(j);
@@ -625,7 +665,7 @@ hz_status hz_batch_take(BatchState* b, uint64_t ticket, hz_status* per_req, uint
   b->jobs.erase(it);
   auto q = std::find(b->queue.begin(), b->queue.end(), j);
   if (q != b->queue.end()) b->queue.erase(q);  // failed at launch, not yet swept
-  free_job(j);
+  free_job(b, j);
   return HZ_OK;
 }
 

@@ -11,8 +11,11 @@ struct BatchState;
 
 BatchState* hz_batch_create(int device, int num_sms, uint64_t mem_budget);
 void hz_batch_destroy(BatchState* b);
+// ordered: the launch that carries the submission first waits for the work
+// enqueued on the cudaStream_t `after` (NULL = the legacy default stream)
+// before this call.
 hz_status hz_batch_submit(BatchState* b, hz_ctx* ctx, const hz_request* reqs, uint32_t count,
-                          uint64_t* ticket);
+                          uint64_t* ticket, bool ordered, void* after);
 hz_status hz_batch_poll(BatchState* b, uint64_t ticket, int64_t timeout_ns, hz_status* per_req,
                         uint64_t* out_lens);
 // Block size used when a caller passes 0 and nothing has been tuned.

@@ -50,6 +50,13 @@ extern "C" hz_status hz_serve_replay(hz_ctx* ctx, const hz_serve_item* items, ui
   cudaGetDevice(&prev);
   cudaSetDevice(hz_ctx_device(ctx));
   BatchState* b = hz_ctx_batch(ctx);
+  // the items' sources may still be written on any stream: the submissions
+  // below are not ordered after the caller's work, so wait for all of it
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    if (prev >= 0) cudaSetDevice(prev);
+    return HZ_ERR_CUDA;
+  }
   hz_batch_track_finished(b, true);
 
   hz::Ring ring(ring_bytes);
@@ -93,7 +100,7 @@ extern "C" hz_status hz_serve_replay(hz_ctx* ctx, const hz_serve_item* items, ui
       waiting.pop_front();
       records[i].submit_s = (double)(now_ns() - t0) * 1e-9;
       uint64_t ticket = 0;
-      const hz_status st = hz_batch_submit(b, ctx, &r, 1, &ticket);
+      const hz_status st = hz_batch_submit(b, ctx, &r, 1, &ticket, false, nullptr);
       if (st != HZ_OK) complete(i, st, 0, 0, now_ns());
       else {
         by_ticket[ticket] = i;

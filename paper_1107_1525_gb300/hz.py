@@ -87,7 +87,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hz_launch_count": (u64, [vp]),
         "hz_profile_read": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
         "hz_kernel_name": (ctypes.c_char_p, [i32]),
-        "hz_submit": (i32, [vp, ctypes.POINTER(HzRequest), u32, ctypes.POINTER(u64)]),
+        "hz_submit": (i32, [vp, ctypes.POINTER(HzRequest), u32, ctypes.POINTER(u64), vp]),
         "hz_poll": (i32, [vp, u64, i64, vp, vp]),
         "hz_compress_noalloc": (i32, [vp, u64, u32, vp, u64, vp, vp, vp]),
         "hz_autotune": (i32, [vp, vp, u64, vp]),
@@ -249,13 +249,15 @@ def hz_decompress_host(ctx: Context, h_in, in_len: int, h_out, out_cap: int, str
     return int(st), int(out_len.value)
 
 
-def hz_submit(ctx: Context, requests) -> int:
-    """requests: sequence of (op, block_size, d_src, src_len, d_dst, dst_cap)."""
+def hz_submit(ctx: Context, requests, stream=None) -> int:
+    """requests: sequence of (op, block_size, d_src, src_len, d_dst, dst_cap); the
+    batch runs after the work queued on `stream` (default: torch's current stream)."""
     arr = (HzRequest * max(1, len(requests)))()
     for i, (op, bs, src, src_len, dst, cap) in enumerate(requests):
         arr[i] = HzRequest(op, bs, _ptr(src), src_len, _ptr(dst), cap)
     ticket = ctypes.c_uint64(0)
-    _check(ctx._lib.hz_submit(ctx.handle, arr, len(requests), ctypes.byref(ticket)), "hz_submit")
+    _check(ctx._lib.hz_submit(ctx.handle, arr, len(requests), ctypes.byref(ticket),
+                              _stream(stream)), "hz_submit")
     return int(ticket.value)
 
 

@@ -55,7 +55,7 @@ def _compress_reqs(hz, bufs, B):
 SIZES = [1, 7, 3000, 4096, 4097, 65_536, 100_000, 1 << 20, 3 * (1 << 20) + 5, 9_000_000]
 
 
-@pytest.mark.parametrize("B", [4096, 65536, 0])
+@pytest.mark.parametrize("B", [4096, 65536, 0, 131072, 1 << 20])
 def test_batched_compress_matches_oracle_and_single_calls(hz, B):
     ctx = hz.Context(0)
     bufs = _buffers(SIZES, seed=1)
@@ -97,6 +97,49 @@ def test_batched_decompress_and_mixed_batch(hz):
         assert np.array_equal(o[:n].cpu().numpy(), oracle.compress(x.cpu().numpy(), 65536))
     for i, (x, d) in enumerate(zip(bufs, dsts2)):
         assert torch.equal(d[: x.numel()], x)
+    ctx.close()
+
+
+@pytest.mark.parametrize("B", [65536, 131072, 1 << 20])
+def test_batched_decompress_of_large_blocks(hz, B):
+    """Streams whose blocks are longer than 64 KiB (the single-buffer decoder
+    gives them a CTA each; the batched one decodes them a warp per block)."""
+    ctx = hz.Context(0)
+    bufs = _buffers([100_000, 1 << 20, 3 * (1 << 20) + 5, 9_000_000], seed=4)
+    streams = [hz.compress(x, B, ctx=ctx) for x in bufs]
+    for x, s in zip(bufs[:2], streams[:2]):
+        assert np.array_equal(s.cpu().numpy(), oracle.compress(x.cpu().numpy(), B))
+    dsts = [torch.empty(x.numel(), dtype=torch.uint8, device=DEV) for x in bufs]
+    reqs = [(hz.HZ_OP_DECOMPRESS, 0, s, s.numel(), d, x.numel()) for s, d, x in
+            zip(streams, dsts, bufs)]
+    per, lens = _run(hz, ctx, reqs)
+    assert list(per) == [0] * len(bufs)
+    for x, d, n in zip(bufs, dsts, lens):
+        assert int(n) == x.numel() and torch.equal(d, x)
+    ctx.close()
+
+
+@pytest.mark.parametrize("plain", [0, 1])
+def test_submission_waits_for_the_callers_stream(hz, plain):
+    """The sources are written on a side stream behind a ~20 ms GPU spin and the
+    requests submitted at once, without a host wait: the batch must see the
+    written data, not the zeros that were there before."""
+    ctx = hz.Context(0)
+    ctx.set_option(hz.HZ_OPT_BATCH_PLAIN, plain)
+    src = _buffers([1 << 20, 3 * (1 << 20) + 5, 100_000], seed=21)
+    xs = [torch.zeros_like(x) for x in src]
+    reqs, outs = _compress_reqs(hz, xs, 65536)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(40_000_000)  # about 20 ms at 2 GHz
+        for x, y in zip(xs, src):
+            x.copy_(y)
+        t = hz.hz_submit(ctx, reqs, stream=side)
+    st, per, lens = hz.hz_poll(ctx, t, len(reqs), -1)
+    assert st == 0 and list(per) == [0] * len(reqs)
+    for x, o, n in zip(src, outs, lens):
+        assert np.array_equal(o[: int(n)].cpu().numpy(), oracle.compress(x.cpu().numpy(), 65536))
     ctx.close()
 
 
