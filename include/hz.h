@@ -187,7 +187,9 @@ hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32_t block_si
 #define HZ_OPT_INDEX 1        /* 1 (default): write the block-offset index */
 #define HZ_OPT_PROFILE 2      /* 1: time every kernel launch with CUDA events */
 #define HZ_OPT_DECODE_LUT_BITS 3  /* decode table width W, 8..12 (default 12) */
-#define HZ_OPT_DECODE_THREADS 4   /* threads per decode CTA: 128, 256 or 512 */
+#define HZ_OPT_DECODE_THREADS 4   /* threads per decode CTA (one warp decodes a block of
+                                     up to 64 KiB; a CTA decodes a larger block):
+                                     128 or 256 (default 256) */
 #define HZ_OPT_AUTOTUNE 5     /* 1 (default): block_size 0 picks the tuned size */
 #define HZ_OPT_BATCH_PLAIN 6  /* 1: hz_submit runs each request through hz_compress /
                                  hz_decompress in turn (the one-launch-per-buffer baseline) */
@@ -202,11 +204,12 @@ int64_t hz_get_option(hz_ctx* ctx, int key);
 /*
  * Autotuner: choose, per input-size class (<= 64 KiB, <= 1 MiB, <= 16 MiB,
  * larger), the block size used when hz_compress / hz_submit get
- * block_size 0, and the decode table width W, by timing compress +
- * decompress round trips of slices of d_sample[0..n) (device memory, the
- * caller's representative data) for B in {4, 8, 16, 32, 64} KiB and W in
- * {10, 11, 12}.  Candidates whose format overhead (Sec. 2.1: 32-63 bits per
- * block) exceeds 1 % of the stream are skipped.  The choice is kept in the
+ * block_size 0, then the decode table width W and the threads per decode
+ * CTA, by timing compress + decompress round trips of slices of
+ * d_sample[0..n) (device memory, the caller's representative data) for B in
+ * {4, 8, 16, 32, 64} KiB, and decompressions of the largest slice for W in
+ * {10, 11, 12} and 128 or 256 threads.  Candidates whose format overhead
+ * (Sec. 2.1: 32-63 bits per block) exceeds 1 % of the stream are skipped.  The choice is kept in the
  * context and, when the environment variable HZ_TUNE_CACHE names a file,
  * written there as JSON; hz_create loads that file when it exists.
  * Synchronous; allocates scratch for the trial streams.

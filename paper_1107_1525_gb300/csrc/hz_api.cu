@@ -256,7 +256,7 @@ hz_status hz_set_option(hz_ctx* c, int key, int64_t v) {
       c->opt_lut_bits = (int)v;
       return HZ_OK;
     case HZ_OPT_DECODE_THREADS:
-      if (v != 128 && v != 256 && v != 512) return HZ_ERR_ARG;
+      if (v != 128 && v != 256) return HZ_ERR_ARG;
       c->opt_dec_threads = (int)v;
       return HZ_OK;
     case HZ_OPT_AUTOTUNE:
@@ -812,13 +812,15 @@ hz_status hz_poll(hz_ctx* c, uint64_t ticket, int64_t timeout_ns, hz_status* per
 
 hz::DevState* hz_ctx_state(hz_ctx* c) { return c->d_state; }
 uint32_t hz_ctx_block_size(hz_ctx* c, uint64_t n) { return autotuned_block(c, n); }
-void hz_ctx_set_tuned(hz_ctx* c, const uint32_t* B, int lut_bits) {
+void hz_ctx_set_tuned(hz_ctx* c, const uint32_t* B, int lut_bits, int dec_threads) {
   for (int k = 0; k < 4; ++k) c->tuned_B[k] = B[k];
   if (lut_bits) c->opt_lut_bits = lut_bits;
+  if (dec_threads) c->opt_dec_threads = dec_threads;
 }
-void hz_ctx_get_tuned(hz_ctx* c, uint32_t* B, int* lut_bits) {
+void hz_ctx_get_tuned(hz_ctx* c, uint32_t* B, int* lut_bits, int* dec_threads) {
   for (int k = 0; k < 4; ++k) B[k] = c->tuned_B[k];
   *lut_bits = c->opt_lut_bits;
+  *dec_threads = c->opt_dec_threads;
 }
 int hz_ctx_device(hz_ctx* c) { return c->device; }
 int hz_ctx_lut_bits(hz_ctx* c) { return c->opt_lut_bits; }

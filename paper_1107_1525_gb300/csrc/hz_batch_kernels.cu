@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(1024) batch_dscan_kernel(BatchCtl* ctl, BatchD
 // ------------------------------------------------------------- block decoding
 __global__ void __launch_bounds__(kFastThreads, 3) batch_decode_kernel(BatchCtl* ctl,
                                                                     const BatchDecomp* decomps) {
-  FastShared& sh = g_fast;
+  FastShared& sh = fast_sh();
   __shared__ uint32_t s_u;
   const uint32_t nunits = ctl->dec_units, n = ctl->ndecomp;
   uint32_t cur = 0xFFFFFFFFu;
@@ -359,6 +359,8 @@ __global__ void batch_clear_kernel(BatchCtl* ctl, const BatchComp* comps,
 void batch_configure() {
   cudaFuncSetAttribute(batch_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sizeof(PackShared));
+  cudaFuncSetAttribute(batch_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fast_smem_bytes(kFastThreads));
 }
 
 void batch_enqueue(const BatchLaunch& L, cudaStream_t s) {
@@ -371,7 +373,8 @@ void batch_enqueue(const BatchLaunch& L, cudaStream_t s) {
   batch_pack_kernel<<<sms * 3, kEncThreads, (int)sizeof(PackShared), s>>>(L.ctl, L.comps);
   batch_dsetup_kernel<<<sms * 2, 256, 0, s>>>(L.ctl, L.decomps);
   batch_dscan_kernel<<<1, 1024, 0, s>>>(L.ctl, L.decomps);
-  batch_decode_kernel<<<sms * 4, kFastThreads, 0, s>>>(L.ctl, L.decomps);
+  batch_decode_kernel<<<sms * 4, kFastThreads, fast_smem_bytes(kFastThreads), s>>>(L.ctl,
+                                                                                 L.decomps);
   batch_finish_kernel<<<sms, 256, 0, s>>>(L.ctl, L.comps, L.decomps, L.results);
 }
 

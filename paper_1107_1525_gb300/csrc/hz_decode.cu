@@ -38,41 +38,60 @@ __global__ void __launch_bounds__(256) decode_setup_kernel(DecodeArgs a, DecTabl
   decode_setup_device(a, T);
 }
 
-// Blocks longer than kFastMaxB: one CTA per block (decode_block_generic), its
-// shared state laid over the fast decoder's, so that no second launch is needed.
+// Blocks longer than kFastMaxB: one CTA of NT threads per block
+// (decode_block_generic), its shared state laid over the fast decoder's, so
+// that no second launch is needed.
+template <int NT>
 struct GenAll {
   GenShared sh;
-  GenBlockShared<kFastThreads> bs;
+  GenBlockShared<NT> bs;
 };
-static_assert(sizeof(GenAll) <= sizeof(FastShared), "the generic state fits the fast one");
 
+template <int NT>
 __device__ __noinline__ void decode_generic_blocks(const DecodeArgs& a, const DecTables* T) {
-  GenAll& g = *reinterpret_cast<GenAll*>(&g_fast);
+  GenAll<NT>& g = *reinterpret_cast<GenAll<NT>*>(g_fast_smem);
   const int W = (int)T->lut_bits;
-  for (int i = threadIdx.x; i < (1 << W); i += kFastThreads) g.sh.lut[i] = T->lut[i];
-  load_canon(g.sh.c, T, threadIdx.x, kFastThreads);
+  for (int i = threadIdx.x; i < (1 << W); i += NT) g.sh.lut[i] = T->lut[i];
+  load_canon(g.sh.c, T, threadIdx.x, NT);
   __syncthreads();
   const uint32_t k_end = a.k_end < g.sh.c.nb ? a.k_end : g.sh.c.nb;
   for (uint32_t k = a.k_begin + blockIdx.x; k < k_end; k += gridDim.x)
-    decode_block_generic<kFastThreads>(a, g.sh, g.bs, k);
+    decode_block_generic<NT>(a, g.sh, g.bs, k);
 }
 
+// Launched with 128 or 256 threads and decode_smem_bytes(threads) of dynamic
+// shared memory.  With at least as many blocks as the launch has warps, warp j
+// of CTA i takes block k_begin + i * warps + j (a CTA's warps read adjacent
+// records), then every (grid * warps)-th after it; with fewer, it takes
+// k_begin + j * grid + i, so that the blocks spread over all CTAs (and so over
+// all SMs) instead of filling a few CTAs' warps.
 __global__ void __launch_bounds__(kFastThreads, 3) decode_fast_kernel(DecodeArgs a,
                                                                   const DecTables* T) {
-  FastShared& sh = g_fast;
   if (!T->ok) return;
   if (!fast_block_size(T->B)) {  // uniform: every CTA takes whole blocks
-    decode_generic_blocks(a, T);
+    if (blockDim.x == 128) decode_generic_blocks<128>(a, T);
+    else decode_generic_blocks<kFastThreads>(a, T);
     return;
   }
-  load_fast_tables(sh, T, threadIdx.x, kFastThreads);
+  const uint32_t warps = blockDim.x / 32;
+  const uint32_t nb = T->nb;
+  const uint32_t k_end = a.k_end < nb ? a.k_end : nb;
+  if (a.k_begin + blockIdx.x >= k_end) return;  // uniform: no block for any warp here
+  const uint32_t warp = threadIdx.x >> 5;
+  const bool spread = k_end - a.k_begin < gridDim.x * warps;
+  const uint32_t k0 = a.k_begin + (spread ? warp * gridDim.x + blockIdx.x : blockIdx.x * warps + warp);
+  FastShared& sh = fast_sh();
+  load_fast_tables(sh, T, threadIdx.x, blockDim.x);
   __syncthreads();
-  const uint32_t warps = kFastThreads / 32;
-  const uint32_t stride = gridDim.x * warps;
   const int mode = fast_mode(T, sh.c);
-  const uint32_t k_end = a.k_end < sh.c.nb ? a.k_end : sh.c.nb;
-  for (uint32_t k = a.k_begin + blockIdx.x * warps + (threadIdx.x >> 5); k < k_end; k += stride)
-    decode_block_fast(a, k, mode);
+  const uint32_t stride = gridDim.x * warps;
+  for (uint32_t k = k0; k < k_end; k += stride) decode_block_fast(a, k, mode);
+}
+
+size_t decode_smem_bytes(int threads) {
+  const size_t fast = fast_smem_bytes(threads);
+  const size_t gen = threads == 128 ? sizeof(GenAll<128>) : sizeof(GenAll<kFastThreads>);
+  return fast > gen ? fast : gen;
 }
 
 // ================================================================ launchers
@@ -83,19 +102,30 @@ cudaError_t launch_decode_setup(const DecodeArgs& a, DecTables* T, cudaStream_t 
 
 cudaError_t launch_decode_blocks(const DecodeArgs& a, const DecTables* T, int threads, int num_sms,
                                  cudaStream_t s) {
-  (void)threads;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_fast_kernel, kFastThreads, 0);
-  if (per_sm < 1) per_sm = 1;
+  if (threads != 128) threads = kFastThreads;
+  const size_t smem = decode_smem_bytes(threads);
+  // the attribute, and the CTAs resident per SM for each width, once per process
+  static bool configured = false;
+  static int per_sm_of[2] = {0, 0};
+  if (!configured) {
+    cudaFuncSetAttribute(decode_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)decode_smem_bytes(kFastThreads));
+    configured = true;
+  }
+  int& per_sm = per_sm_of[threads == 128 ? 0 : 1];
+  if (per_sm < 1) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_fast_kernel, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+  }
   uint64_t grid = (uint64_t)num_sms * per_sm;
   // a block range shorter than the resident warps needs fewer CTAs (the
   // block count itself is only known on the device: an unbounded range keeps
   // the full grid)
   if (a.k_end != 0xFFFFFFFFu) {
-    const uint64_t need = ((uint64_t)(a.k_end - a.k_begin) + kFastThreads / 32 - 1) / (kFastThreads / 32);
+    const uint64_t need = ((uint64_t)(a.k_end - a.k_begin) + threads / 32 - 1) / (threads / 32);
     if (need < grid) grid = need ? need : 1;
   }
-  decode_fast_kernel<<<(unsigned)grid, kFastThreads, 0, s>>>(a, T);
+  decode_fast_kernel<<<(unsigned)grid, threads, smem, s>>>(a, T);
   return cudaGetLastError();
 }
 

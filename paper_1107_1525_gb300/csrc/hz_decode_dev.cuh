@@ -515,14 +515,27 @@ struct FastShared {
   uint32_t lut[kFastLutWords];
   uint32_t has_l2, fill_k, lut_rep;
   CanonTables c;
-  __align__(16) uint32_t ring[kFastThreads * kRingStride];
 };
 
-// The fast decoders' shared state, one per CTA of any kernel that uses it.  The
-// block decoders below are separate (not inlined) functions, so that each gets
-// its own register allocation; they reach the tables through this symbol, not a
-// parameter, so that their accesses stay shared-memory loads.
-static __shared__ FastShared g_fast;
+// The fast decoders' shared state, one per CTA of any kernel that uses it, in
+// the launch's dynamic shared memory: the tables, then kRingStride words of
+// payload ring per thread, so that the size follows the CTA's width (128 or
+// 256 threads).  The block decoders below are separate (not inlined)
+// functions, so that each gets its own register allocation; they reach the
+// state through this symbol, not a parameter, so that their accesses stay
+// shared-memory loads.
+constexpr size_t kFastRingOffset = (sizeof(FastShared) + 15) & ~(size_t)15;
+static __host__ __device__ constexpr size_t fast_smem_bytes(int threads) {
+  return kFastRingOffset + (size_t)threads * kRingStride * 4;
+}
+extern __shared__ __align__(16) uint8_t g_fast_smem[];
+static __device__ __forceinline__ FastShared& fast_sh() {
+  return *reinterpret_cast<FastShared*>(g_fast_smem);
+}
+// this thread's payload ring
+static __device__ __forceinline__ uint32_t* fast_ring() {
+  return reinterpret_cast<uint32_t*>(g_fast_smem + kFastRingOffset) + threadIdx.x * kRingStride;
+}
 
 // The lookup tables of T into shared memory (all threads of the CTA).
 static __device__ __forceinline__ void load_fast_tables(FastShared& sh, const DecTables* T,
@@ -812,7 +825,7 @@ __device__ __forceinline__ uint32_t ring_take(const FastShared& sh, RingWin& w, 
 
 template <int kMode>
 __device__ __noinline__ void decode_block_warp(const DecodeArgs& a, uint32_t k) {
-  FastShared& sh = g_fast;
+  FastShared& sh = fast_sh();
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t W = sh.c.W;
   RecInfo r;
@@ -832,7 +845,7 @@ __device__ __noinline__ void decode_block_warp(const DecodeArgs& a, uint32_t k) 
   g.p = reinterpret_cast<const uint32_t*>(payload);
   g.nw = nw;
   RingWin w;
-  w.setup(payload, a.in + a.in_len, sh.ring + threadIdx.x * kRingStride);
+  w.setup(payload, a.in + a.in_len, fast_ring());
   const uint32_t Lw = (nw + 31) / 32;
   const uint32_t L = Lw * 32;
   const uint32_t nsub = (bits + L - 1) / L;
@@ -1015,7 +1028,7 @@ static __device__ __forceinline__ void skip_symbol0(const FastShared& sh, GWin& 
 
 template <int K1, int K2, bool kRep>
 __device__ __noinline__ void decode_block_warp0(const DecodeArgs& a, uint32_t k) {
-  FastShared& sh = g_fast;
+  FastShared& sh = fast_sh();
   constexpr uint32_t kCap = K1 == 3 ? 10u : (uint32_t)kLutMaxBits;  // bits per counting step
   constexpr uint32_t kG1 = K1 == 3 ? 15u : 16u;                      // counting steps per refill
   const uint32_t lane = threadIdx.x & 31;
@@ -1038,7 +1051,7 @@ __device__ __noinline__ void decode_block_warp0(const DecodeArgs& a, uint32_t k)
   g.p = reinterpret_cast<const uint32_t*>(payload);
   g.nw = nw;
   RingWin w;
-  w.setup(payload, a.in + a.in_len, sh.ring + threadIdx.x * kRingStride);
+  w.setup(payload, a.in + a.in_len, fast_ring());
   const uint32_t Lw = (nw + 31) / 32;
   const uint32_t L = Lw * 32;
   const uint32_t nsub = (bits + L - 1) / L;
@@ -1196,8 +1209,8 @@ static __device__ __forceinline__ int fast_mode(const DecTables* T, const CanonT
 static __device__ __forceinline__ void decode_block_fast(const DecodeArgs& a,
                                                          uint32_t k, int mode) {
   if (mode == 0) {
-    if (g_fast.fill_k == 4) decode_block_warp0<3, 4, true>(a, k);
-    else if (g_fast.fill_k == 3) decode_block_warp0<3, 3, true>(a, k);
+    if (fast_sh().fill_k == 4) decode_block_warp0<3, 4, true>(a, k);
+    else if (fast_sh().fill_k == 3) decode_block_warp0<3, 3, true>(a, k);
     else decode_block_warp0<2, 2, false>(a, k);
   } else if (mode == 1) decode_block_warp<1>(a, k);
   else decode_block_warp<2>(a, k);

@@ -4,8 +4,8 @@
 // Per input-size class it times compress + decompress round trips of a slice
 // of the caller's sample for every candidate block size, keeps the fastest
 // one whose per-block format overhead stays within 1 % (Sec. 2.1: each block
-// costs 32-63 bits), and then times the decoder's table width on the largest
-// class.  The result lives in the context; HZ_TUNE_CACHE names a file that
+// costs 32-63 bits), and then times the decoder's table width and its CTA
+// width on the largest class.  The result lives in the context; HZ_TUNE_CACHE names a file that
 // stores it across processes.
 #include <stdio.h>
 #include <stdlib.h>
@@ -14,8 +14,8 @@
 #include "hz_internal.cuh"
 
 uint32_t hz_ctx_block_size(hz_ctx* c, uint64_t n);
-void hz_ctx_set_tuned(hz_ctx* c, const uint32_t* B, int lut_bits);
-void hz_ctx_get_tuned(hz_ctx* c, uint32_t* B, int* lut_bits);
+void hz_ctx_set_tuned(hz_ctx* c, const uint32_t* B, int lut_bits, int dec_threads);
+void hz_ctx_get_tuned(hz_ctx* c, uint32_t* B, int* lut_bits, int* dec_threads);
 int hz_ctx_device(hz_ctx* c);
 
 namespace {
@@ -23,14 +23,17 @@ namespace {
 constexpr uint64_t kClassSize[4] = {64ull << 10, 1ull << 20, 16ull << 20, 256ull << 20};
 constexpr uint32_t kCandB[5] = {4096, 8192, 16384, 32768, 65536};
 constexpr int kCandW[3] = {10, 11, 12};
+constexpr int kCandThreads[2] = {256, 128};
 
-void write_cache(const uint32_t* B, int W) {
+void write_cache(const uint32_t* B, int W, int T) {
   const char* path = getenv("HZ_TUNE_CACHE");
   if (!path || !*path) return;
   FILE* f = fopen(path, "w");
   if (!f) return;
-  fprintf(f, "{\"version\": 1, \"block_size\": [%u, %u, %u, %u], \"lut_bits\": %d}\n", B[0], B[1],
-          B[2], B[3], W);
+  fprintf(f,
+          "{\"version\": 1, \"block_size\": [%u, %u, %u, %u], \"lut_bits\": %d, "
+          "\"dec_threads\": %d}\n",
+          B[0], B[1], B[2], B[3], W, T);
   fclose(f);
 }
 
@@ -46,16 +49,18 @@ void hz_tune_load_cache(hz_ctx* c) {
   fclose(f);
   buf[got] = 0;
   uint32_t B[4];
-  int W = 0;
+  int W = 0, T = 0;
   const char* p = strstr(buf, "\"block_size\"");
   const char* q = strstr(buf, "\"lut_bits\"");
+  const char* t = strstr(buf, "\"dec_threads\"");  // absent from older files: keep the default
   if (!p || !q) return;
   if (sscanf(p, "\"block_size\": [%u, %u, %u, %u]", &B[0], &B[1], &B[2], &B[3]) != 4) return;
   if (sscanf(q, "\"lut_bits\": %d", &W) != 1) return;
+  if (t && (sscanf(t, "\"dec_threads\": %d", &T) != 1 || (T != 128 && T != 256))) return;
   for (int k = 0; k < 4; ++k)
     if (B[k] == 0 || B[k] > hz::kMaxBlock) return;
   if (W < hz::kLutMinBits || W > hz::kLutMaxBits) return;
-  hz_ctx_set_tuned(c, B, W);
+  hz_ctx_set_tuned(c, B, W, T);
 }
 
 extern "C" hz_status hz_autotune(hz_ctx* c, const uint8_t* d_sample, uint64_t n, void* stream) {
@@ -71,10 +76,10 @@ extern "C" hz_status hz_autotune(hz_ctx* c, const uint8_t* d_sample, uint64_t n,
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   hz_status result = HZ_OK;
   uint32_t best_B[4];
-  int best_W = 12;
+  int best_W = 12, best_T = 256;
   uint32_t old_B[4];
-  int old_W = 12;
-  hz_ctx_get_tuned(c, old_B, &old_W);
+  int old_W = 12, old_T = 256;
+  hz_ctx_get_tuned(c, old_B, &old_W, &old_T);
   if (cudaMalloc(&d_out, cap) != cudaSuccess || cudaMalloc(&d_dec, m_max) != cudaSuccess ||
       cudaMalloc(&d_len, 2 * sizeof(uint64_t)) != cudaSuccess ||
       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -126,26 +131,42 @@ extern "C" hz_status hz_autotune(hz_ctx* c, const uint8_t* d_sample, uint64_t n,
     uint64_t len = 0;
     hz_compress(c, d_sample, m, best_B[3], nullptr, d_out, cap, d_len, s);
     cudaMemcpyAsync(&len, d_len, 8, cudaMemcpyDeviceToHost, s);
+    // eight decompressions after a warm-up, in ms (1e30 if one failed)
+    auto time_decode = [&]() -> float {
+      float ms = 0;
+      hz_decompress(c, d_out, len, d_dec, m, d_len + 1, s);
+      cudaEventRecord(e0, s);
+      for (int it = 0; it < 8; ++it) hz_decompress(c, d_out, len, d_dec, m, d_len + 1, s);
+      cudaEventRecord(e1, s);
+      if (hz_sync(c, s) != HZ_OK) return 1e30f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      return ms;
+    };
     if (hz_sync(c, s) == HZ_OK) {
+      hz_set_option(c, HZ_OPT_DECODE_THREADS, 256);
       for (int W : kCandW) {
         hz_set_option(c, HZ_OPT_DECODE_LUT_BITS, W);
-        float ms = 0;
-        hz_decompress(c, d_out, len, d_dec, m, d_len + 1, s);  // warm-up
-        cudaEventRecord(e0, s);
-        for (int it = 0; it < 8; ++it) hz_decompress(c, d_out, len, d_dec, m, d_len + 1, s);
-        cudaEventRecord(e1, s);
-        if (hz_sync(c, s) != HZ_OK) continue;
-        cudaEventElapsedTime(&ms, e0, e1);
+        const float ms = time_decode();
         if (ms < best) {
           best = ms;
           best_W = W;
         }
       }
+      hz_set_option(c, HZ_OPT_DECODE_LUT_BITS, best_W);
+      best = 1e30f;
+      for (int T : kCandThreads) {
+        hz_set_option(c, HZ_OPT_DECODE_THREADS, T);
+        const float ms = time_decode();
+        if (ms < best) {
+          best = ms;
+          best_T = T;
+        }
+      }
     }
-    hz_ctx_set_tuned(c, best_B, best_W);
-    write_cache(best_B, best_W);
+    hz_ctx_set_tuned(c, best_B, best_W, best_T);
+    write_cache(best_B, best_W, best_T);
   } else {
-    hz_ctx_set_tuned(c, old_B, old_W);
+    hz_ctx_set_tuned(c, old_B, old_W, old_T);
   }
   cudaFree(d_out);
   cudaFree(d_dec);

@@ -246,6 +246,8 @@ def test_autotune_and_cache(hz, tmp_path):
         assert all(b in (4096, 8192, 16384, 32768, 65536) for b in chosen)
         W = ctx.get_option(hz.HZ_OPT_DECODE_LUT_BITS)
         assert W in (10, 11, 12)
+        T = ctx.get_option(hz.HZ_OPT_DECODE_THREADS)
+        assert T in (128, 256)
         assert os.path.exists(path)
         ctx.close()
         # a new context picks the choice up from the cache
@@ -253,6 +255,7 @@ def test_autotune_and_cache(hz, tmp_path):
         assert [lib.hz_tuned_block_size(ctx2.handle, n) for n in (1 << 16, 1 << 20, 16 << 20,
                                                                   64 << 20)] == chosen
         assert ctx2.get_option(hz.HZ_OPT_DECODE_LUT_BITS) == W
+        assert ctx2.get_option(hz.HZ_OPT_DECODE_THREADS) == T
         # block_size 0 uses it, and the stream is the oracle's for that block size
         y = x[: 3 << 20]
         s = hz.compress(y, 0, ctx=ctx2)

@@ -130,3 +130,38 @@ def test_small_blocks(hz, name, B):
     assert np.array_equal(s.cpu().numpy(), oracle.compress(x, B, lengths=lengths))
     assert torch.equal(hz.decompress(s, ctx=ctx), xd)
     ctx.close()
+
+
+@pytest.mark.parametrize("threads", [128, 256])
+@pytest.mark.parametrize("name", ["chain10", "chain12", "chain14", "chain40", "incomplete"])
+def test_decode_cta_width(hz, threads, name):
+    """Both decoder CTA widths give the oracle's data: streams of a few blocks
+    (spread one per CTA), many blocks (several per warp), ragged tails, and
+    blocks over 64 KiB (one CTA per block).  chain40 (longest code 40 bits)
+    takes the decoder that reads codes over 32 bits from memory; every code
+    length occurs."""
+    lengths = _chain(40) if name == "chain40" else CODES[name]
+    longest = np.nonzero(lengths == lengths.max())[0]
+    codes = hz.make_codes(lengths, oracle.canonical_codes(lengths))
+    ctx = hz.Context(0)
+    ctx.set_option(hz.HZ_OPT_DECODE_THREADS, threads)
+    assert ctx.get_option(hz.HZ_OPT_DECODE_THREADS) == threads
+    for B, n, seed in ((4096, 5 * 4096 + 17, 1), (65536, 300 * 65536 + 5, 2),
+                       (1000, 3_000_001, 3), (131072, 5 * 131072 + 999, 4)):
+        x = _sample(lengths, n, seed + threads)
+        x[::9973] = longest[np.arange(len(x[::9973])) % len(longest)]
+        xd = torch.from_numpy(x).to(DEV)
+        s = hz.compress(xd, B, ctx=ctx, codes=codes)
+        if n < 4_000_000:
+            assert np.array_equal(s.cpu().numpy(), oracle.compress(x, B, lengths=lengths)), B
+        assert torch.equal(hz.decompress(s, ctx=ctx), xd), (name, threads, B)
+    ctx.close()
+
+
+def test_decode_threads_option_values(hz):
+    ctx = hz.Context(0)
+    for bad in (0, 64, 512, 1024):
+        with pytest.raises(hz.HzError):
+            ctx.set_option(hz.HZ_OPT_DECODE_THREADS, bad)
+    assert ctx.get_option(hz.HZ_OPT_DECODE_THREADS) == 256
+    ctx.close()
