@@ -50,8 +50,8 @@ WORKLOADS = {
 # ncu captures of the current kernel revisions on the 256 MiB profiling case,
 # scaled by the units processed to a 1 GiB launch (profiles/*.md); other
 # workloads report null.
-NCU_TRAFFIC = {"mixed-1GiB": {"decode": 4 * (455_402_752 + 251_671_808),
-                              "encode_pack": 4 * (269_589_504 + 165_645_312)}}
+NCU_TRAFFIC = {"mixed-1GiB": {"decode": 4 * (453_267_968 + 250_598_144),
+                              "encode_pack": 4 * (269_556_480 + 166_418_432)}}
 
 
 def load_peaks():
