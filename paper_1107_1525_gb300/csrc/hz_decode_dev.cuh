@@ -117,7 +117,6 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   if (t == 0) {
     T->ok = 0;
     T->needs_chase = 0;
-    a.st->dec_deferred = 0;
     s_ok = a.in_len >= kHeaderBytes;
   }
   if (t <= kMaxLen) cnt[t] = 0;
@@ -372,8 +371,6 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
     T->lut_rep = rep ? 1u : 0u;
     *a.out_len = n;
     if (!cap_ok) set_error(a.st, HZ_ERR_CAPACITY, 0x302);
-    // blocks too large for the fast kernel all go to the generic one
-    if (B > 65536) a.st->dec_deferred = nb;
   }
   if (!cap_ok) return;  // uniform
   __syncthreads();
@@ -489,10 +486,6 @@ constexpr int kFastThreads = 256;
 
 static __host__ __device__ __forceinline__ bool fast_block_size(uint32_t B) { return B <= kFastMaxB; }
 
-static __device__ __forceinline__ bool fast_capable(uint32_t B, uint32_t nw) {
-  (void)nw;
-  return fast_block_size(B);
-}
 
 // Per lane, a ring of kRingSlots slots of 32 bytes of its payload range in
 // shared memory, fed by cp.async.  Refills happen at warp-uniform points,
@@ -1279,9 +1272,8 @@ __device__ void decode_block_generic(const DecodeArgs& a, const GenShared& sh,
   __syncthreads();  // every thread is done with the previous block's shared state
   if (t == 0) {
     bs.r = read_record(a, sh.c, k);
-    // corrupt records are reported by the fast kernel unless it never ran
-    bs.ok = bs.r.ok && !fast_capable(sh.c.B, bs.r.nw) ? 1 : 0;
-    if (!bs.r.ok && !fast_block_size(sh.c.B)) set_error(a.st, HZ_ERR_CORRUPT, 0x310);
+    bs.ok = bs.r.ok ? 1 : 0;
+    if (!bs.r.ok) set_error(a.st, HZ_ERR_CORRUPT, 0x310);
   }
   __syncthreads();
   if (!bs.ok) return;  // uniform

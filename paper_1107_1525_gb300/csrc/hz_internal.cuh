@@ -57,8 +57,7 @@ constexpr int kMaxScanCtas = (int)((1ull << 32) / kEncTile / kScanTilesPerCta); 
 struct DevState {
   uint32_t error;           // first error recorded (as -hz_status), 0 = none
   uint32_t error_where;     // kernel-specific detail for debugging
-  uint32_t dec_deferred;    // blocks decoded one CTA per block (blocks over 64 KiB)
-  uint32_t pad0;
+  uint32_t pad0[2];
   // ---- cleared before every compress (one memset from here to `codes`)
   uint32_t tile_counter;    // ticket of the scan CTAs
   uint32_t enc_ok;          // set by the encoder's scan: 1 when the stream fits the output
