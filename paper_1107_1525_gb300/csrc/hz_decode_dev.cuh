@@ -707,8 +707,7 @@ struct RingWin {
 // to 32 bits: a longer code is decoded from the window itself (filled before
 // every step, so it holds more than 32 bits), through the second-level table
 // when there is one; kMode 2 -- any length: a longer code is read straight
-// from memory and restarts the window.  (decode_block_warp's kMode 0 branches
-// serve no caller now.)
+// from memory and restarts the window.
 
 // 64-bit window over the payload words read straight from global memory
 // (through L1), refilled one word at a time: the fix-up's short walks and
@@ -784,9 +783,10 @@ static __device__ __forceinline__ uint32_t long_code(const FastShared& sh, uint3
 template <int kMode>
 __device__ __forceinline__ uint32_t ring_step(const FastShared& sh, RingWin& w, uint32_t& pos,
                                               uint32_t W, const GWin& g, bool& bad) {
+  static_assert(kMode == 1 || kMode == 2, "mode 0 has its own decoder");
   const uint32_t e = sh.lut[w.peek(W)];
   const uint32_t l0 = e_l0(e);
-  if (kMode == 0 || l0) {
+  if (l0) {
     pos += l0;
     w.consume(l0);
     return e & 0xFFu;
@@ -962,7 +962,7 @@ __device__ __noinline__ void decode_block_warp(const DecodeArgs& a, uint32_t k) 
           uint32_t word = 0;
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
-            if (kMode != 0 || (b & 1) == 0) w.fill();  // kMode 0: two steps of <= 12 bits follow
+            w.fill();
             word |= ring_step<kMode>(sh, w, pos, W, g, bad) << (8 * b);
           }
           q[j] = word;

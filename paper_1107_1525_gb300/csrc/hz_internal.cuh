@@ -95,7 +95,7 @@ enum KernelId : int32_t {
   K_ENC_PACK = 4,
   K_DECODE_SETUP = 5,
   K_DECODE = 6,
-  K_DECODE_GENERIC = 7,
+  K_DECODE_GENERIC = 7,  // not launched any more (decode_fast_kernel takes large blocks); id kept
   K_BATCH = 8,
   K_DECODE_CHASE = 9,
   K_COUNT
