@@ -27,7 +27,11 @@
  * Readings taken where the paper is silent (each one is listed in the design
  * notes of the repository):
  *   R1 tie-break: nodes are ordered by (weight, id); a leaf's id is its byte
- *      value, the t-th merged node gets id 256 + t.
+ *      value, the t-th merged node gets id 256 + t.  The paper states no
+ *      tie-break, so which of several optimal length sets this picks is
+ *      parity unpinned: the tests pin the code cost (brute force, Kraft,
+ *      closed forms), check that the heap and two-queue forms agree, and
+ *      compare one hand-derived case with ties.
  *   R2 code values: canonical assignment from the lengths (RFC 1951 3.2.2
  *      convention) instead of left=0/right=1 tree paths; lengths, and so the
  *      compressed size, are the same.
