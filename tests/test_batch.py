@@ -207,6 +207,47 @@ def test_admission_budget(hz):
     ctx.close()
 
 
+def test_batched_workload_full_size(hz):
+    """The bench's batched workload at full size, in the bench's launch shape:
+    4096 buffers, lengths log-uniform in [4 KiB, 16 MiB] (about 8.2 GB), Zipf(s_i)
+    bytes, tuned block sizes, all in one submission out of one arena.  Every
+    buffer must come back from the batched decompression; a sample of 24
+    streams (the largest and smallest among them) must be the oracle's, byte
+    for byte."""
+    lens, s = datagen.batch_sizes(count=4096, seed=3)
+    offs = np.zeros(len(lens) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum((lens + 255) // 256 * 256)
+    arena = torch.empty(int(offs[-1]), dtype=torch.uint8, device=DEV)
+    for i in range(len(lens)):
+        arena[offs[i]:offs[i] + lens[i]] = datagen.sample_iid(
+            datagen.zipf_pmf(float(s[i])), int(lens[i]), (3 << 20) + i, DEV)
+    ctx = hz.Context(0)
+    lib = hz.load_library()
+    Bs = [lib.hz_tuned_block_size(ctx.handle, int(n)) for n in lens]
+    caps = np.array([hz.hz_compress_bound(int(n), int(b)) for n, b in zip(lens, Bs)])
+    coffs = np.zeros(len(lens) + 1, dtype=np.int64)
+    coffs[1:] = np.cumsum((caps + 255) // 256 * 256)
+    out = torch.empty(int(coffs[-1]), dtype=torch.uint8, device=DEV)
+    back = torch.zeros_like(arena)
+    creqs = [(hz.HZ_OP_COMPRESS, 0, arena.data_ptr() + int(offs[i]), int(lens[i]),
+              out.data_ptr() + int(coffs[i]), int(caps[i])) for i in range(len(lens))]
+    per, slen = _run(hz, ctx, creqs)
+    assert (per == 0).all()
+    dreqs = [(hz.HZ_OP_DECOMPRESS, 0, out.data_ptr() + int(coffs[i]), int(slen[i]),
+              back.data_ptr() + int(offs[i]), int(lens[i])) for i in range(len(lens))]
+    per, dl = _run(hz, ctx, dreqs)
+    assert (per == 0).all() and (dl.astype(np.int64) == lens).all()
+    assert torch.equal(back, arena)
+    order = np.argsort(lens)
+    rng = np.random.default_rng(5)
+    pick = set(order[:2]) | set(order[-2:]) | set(rng.choice(len(lens), 20, replace=False))
+    for i in sorted(pick):
+        x = arena[int(offs[i]):int(offs[i]) + int(lens[i])].cpu().numpy()
+        got = out[int(coffs[i]):int(coffs[i]) + int(slen[i])].cpu().numpy()
+        assert np.array_equal(got, oracle.compress(x, int(Bs[i]))), i
+    ctx.close()
+
+
 def test_batched_workload_sample(hz):
     """The 4096-buffer workload's size and skew mix, at 128 buffers of up to 1 MiB."""
     lens, s = datagen.batch_sizes(count=128, lo=4096, hi=1 << 20, seed=3)
