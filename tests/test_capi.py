@@ -70,5 +70,7 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.hz_decompress(None, None, 0, None, 0, None, None) == -1
     assert lib.hz_sync(None, None) == -1
     assert lib.hz_set_option(None, 1, 1) == -1
+    assert lib.hz_submit(None, None, 0, None, None) == -1
+    assert lib.hz_poll(None, 1, 0, None, None) == -1
     assert lib.hz_launch_count(None) == 0
     assert lib.hz_kernel_name(4) == b"encode_pack"
