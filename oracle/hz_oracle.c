@@ -6,7 +6,8 @@
  * TEST INFRASTRUCTURE ONLY.  This file is the checker the GPU library is
  * compared against.  Only the test suite, the smoke check and the benchmark's
  * CPU-baseline leg may load it.  It shares no code, header, table or helper
- * with the CUDA library, and it includes nothing but the C standard library.
+ * with the CUDA library, and it includes nothing but the C standard library
+ * and its own declarations (hz_oracle.h).
  *
  * What the paper fixes, and where:
  *   - Sec. 2 (Huffman Compression): count every distinct symbol of the
@@ -45,19 +46,33 @@
  *   R7 a buffer with a single distinct symbol codes it with length 1, code 0.
  *   R8 n = 0 gives no blocks and a header-only stream.
  *   R9 the last block holds the remaining n - (nb-1)*B symbols.
+ *   R14 sub-block offsets (flags bit 1, only with bit 0): Sec. 2.1 makes
+ *      blocks decodable in parallel through a table of offsets; the same kind
+ *      of table one level down gives, for every S symbols inside a block, the
+ *      payload bit at which that symbol's code starts, so that parts of one
+ *      block can be decoded in parallel too.  The records themselves are
+ *      unchanged; the table is an optional container section like the index.
+ *      S is a multiple of 32 that divides B.
  *
  * Container layout (all integers little-endian):
- *   0   "HZB1"             4   u32 flags (bit 0: block-offset index present)
+ *   0   "HZB1"             4   u32 flags (bit 0: block-offset index present,
+ *                                         bit 1: sub-block offsets present)
  *   8   u64 n              16  u32 B (symbols per block)     20 u32 nb
  *   24  u8 len[256]        280 u32 word_offset[nb] if flags bit 0
+ *   then, if flags bit 1: u32 S, and for every block k the M - 1 entries
+ *       u32 sub_offset[k][j], j = 1 .. M - 1, M = B / S: the payload bit
+ *       offset in record k of the code of the block's symbol j*S, or bits_k
+ *       when the block holds no symbol j*S (only in the last block)
  *   then the block records back to back, each
  *       u32 bits_k, ceil(bits_k/32) payload words.
  *   word_offset[k] is the position of record k, in 32-bit words, counted from
- *   the first byte after the index.
+ *   the first byte after the index sections.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include "hz_oracle.h"
 
 #define OR_OK 0
 #define OR_ERR_ARG (-1)
@@ -69,6 +84,7 @@
 #define OR_MAX_LEN 64
 #define OR_MAX_BLOCK (1u << 24)
 #define OR_FLAG_INDEX 1u
+#define OR_FLAG_SUB 2u
 
 /* ---------------------------------------------------------------- helpers */
 
@@ -298,14 +314,56 @@ uint64_t oracle_encode_block(const uint8_t* x, uint64_t count, const uint8_t* le
 /* ---------------------------------------------- the whole compressed stream */
 
 /*
+ * Reading R14: the sub-block offsets of one block of `count` symbols -- entry
+ * j - 1 (j = 1 .. M - 1) is the sum of the code lengths of the block's first
+ * j*S symbols, i.e. the payload bit where the code of symbol j*S starts, or
+ * the block's whole payload length when the block has no symbol j*S.
+ */
+void oracle_sub_offsets(const uint8_t* x, uint64_t count, const uint8_t* len, uint32_t S,
+                        uint32_t M, uint32_t* entries) {
+  for (uint32_t j = 1; j < M; ++j) {
+    uint64_t upto = (uint64_t)j * S < count ? (uint64_t)j * S : count;
+    entries[j - 1] = (uint32_t)oracle_block_bits(x, upto, len);
+  }
+}
+
+/* Flags and sub-block size a stream may carry: bit 1 only with bit 0, and S a
+ * multiple of 32 dividing B. */
+int oracle_layout_ok(uint32_t flags, uint32_t B, uint32_t S) {
+  if (flags & ~(OR_FLAG_INDEX | OR_FLAG_SUB)) return 0;
+  if (flags & OR_FLAG_SUB) {
+    if (!(flags & OR_FLAG_INDEX)) return 0;
+    if (S < 32 || S % 32 != 0 || B % S != 0) return 0;
+  }
+  return 1;
+}
+
+/* Where record k's sub-block offsets sit in stream s (NULL without flags
+ * bit 1): after the header, the index and the section's S word. */
+const uint8_t* oracle_sub_entries(const uint8_t* s, uint32_t nb, uint32_t B, uint32_t flags,
+                                  uint32_t S, uint64_t k) {
+  if (!(flags & OR_FLAG_SUB)) return NULL;
+  return s + OR_HEADER_BYTES + 4ull * nb + 4 + 4ull * k * (B / S - 1);
+}
+
+/* Bytes before the first record: header, index, sub-block section. */
+uint64_t oracle_records_at(uint64_t nb, uint32_t B, uint32_t flags, uint32_t S) {
+  uint64_t at = OR_HEADER_BYTES;
+  if (flags & OR_FLAG_INDEX) at += 4 * nb;
+  if (flags & OR_FLAG_SUB) at += 4 + 4 * nb * (uint64_t)(B / S - 1);
+  return at;
+}
+
+/*
  * Size in bytes of the stream for x under `len` (no data is written):
- * header, optional index, and per block 4 * (1 + ceil(bits_k / 32)).
+ * header, index sections, and per block 4 * (1 + ceil(bits_k / 32)).
  */
 int oracle_stream_size(const uint8_t* x, uint64_t n, uint32_t B, const uint8_t* len,
-                       uint32_t flags, uint64_t* size) {
-  if (B == 0 || B > OR_MAX_BLOCK || n > 0xFFFFFFFFull) return OR_ERR_ARG;
+                       uint32_t flags, uint32_t S, uint64_t* size) {
+  if (B == 0 || B > OR_MAX_BLOCK || n > 0xFFFFFFFFull || !oracle_layout_ok(flags, B, S))
+    return OR_ERR_ARG;
   uint64_t nb = ceil_div(n, B);
-  uint64_t total = OR_HEADER_BYTES + ((flags & OR_FLAG_INDEX) ? 4 * nb : 0);
+  uint64_t total = oracle_records_at(nb, B, flags, S);
   for (uint64_t k = 0; k < nb; ++k) {
     uint64_t lo = k * B, hi = lo + B < n ? lo + B : n;
     uint64_t bits = oracle_block_bits(x + lo, hi - lo, len);
@@ -316,84 +374,129 @@ int oracle_stream_size(const uint8_t* x, uint64_t n, uint32_t B, const uint8_t* 
 }
 
 /*
- * Compress x[0..n) with blocks of B symbols.  `given_len` may be NULL (build
- * the code from x's histogram, Sec. 2) or a 256-entry length table that must
- * be a prefix code covering every symbol present in x.  flags: bit 0 writes
- * the block-offset index.  On OR_ERR_CAPACITY, *out_len holds the size needed.
+ * The code a stream is written with: `given_len` (which must cover every
+ * symbol present in x) or, when NULL, the Huffman code of x's histogram
+ * (Sec. 2); then its canonical values (R2).
  */
-int oracle_compress(const uint8_t* x, uint64_t n, uint32_t B, const uint8_t* given_len,
-                    uint32_t flags, uint8_t* out, uint64_t cap, uint64_t* out_len) {
-  uint8_t len[256];
-  uint64_t code[256];
-  *out_len = 0;
-  if (B == 0 || B > OR_MAX_BLOCK || n > 0xFFFFFFFFull || (flags & ~OR_FLAG_INDEX))
-    return OR_ERR_ARG;
+int oracle_stream_code(const uint8_t* x, uint64_t n, const uint8_t* given_len, uint8_t* len,
+                       uint64_t* code) {
+  uint64_t freq[256];
+  oracle_histogram(x, n, freq);
   if (given_len) {
     memcpy(len, given_len, 256);
-    uint64_t freq[256];
-    oracle_histogram(x, n, freq);
     for (int s = 0; s < 256; ++s)
       if (freq[s] > 0 && len[s] == 0) return OR_ERR_ARG;
   } else {
-    uint64_t freq[256];
-    oracle_histogram(x, n, freq);
     int st = oracle_code_lengths(freq, len);
     if (st != OR_OK) return st;
   }
   if (oracle_canonical_codes(len, code) != OR_OK) return OR_ERR_ARG;
+  return OR_OK;
+}
+
+/* The 280-byte header (R5): magic, flags, n, B, nb, the code lengths; and,
+ * with flags bit 1, the sub-block size S at the start of its section. */
+void oracle_write_header(uint8_t* out, uint64_t n, uint32_t B, uint32_t nb, uint32_t flags,
+                         uint32_t S, const uint8_t* len) {
+  memset(out, 0, OR_HEADER_BYTES);
+  memcpy(out, "HZB1", 4);
+  put_u32(out + 4, flags);
+  put_u64(out + 8, n);
+  put_u32(out + 16, B);
+  put_u32(out + 20, nb);
+  memcpy(out + 24, len, 256);
+  if (flags & OR_FLAG_SUB)
+    put_u32(out + OR_HEADER_BYTES + ((flags & OR_FLAG_INDEX) ? 4ull * nb : 0), S);
+}
+
+/*
+ * Block k of x (Sec. 2.1, Figs. 3-4) into the stream `out`: its record at
+ * word `word_off` of the record area, its index entry (flags bit 0) and its
+ * sub-block offsets (flags bit 1, R14).  Returns OR_OK or OR_ERR_NOMEM.
+ */
+int oracle_write_block(uint8_t* out, const uint8_t* x, uint64_t n, uint32_t B, uint32_t nb,
+                       uint32_t flags, uint32_t S, const uint8_t* len, const uint64_t* code,
+                       uint64_t k, uint64_t word_off) {
+  uint64_t lo = k * B, hi = lo + B < n ? lo + B : n;
+  uint64_t need = 1 + ceil_div(oracle_block_bits(x + lo, hi - lo, len), 32);
+  uint32_t* rec = (uint32_t*)malloc(need * sizeof(uint32_t));
+  if (!rec) return OR_ERR_NOMEM;
+  uint64_t got = oracle_encode_block(x + lo, hi - lo, len, code, rec, need);
+  uint64_t blocks_at = oracle_records_at(nb, B, flags, S);
+  for (uint64_t w = 0; w < got; ++w) put_u32(out + blocks_at + 4 * (word_off + w), rec[w]);
+  free(rec);
+  if (flags & OR_FLAG_INDEX) put_u32(out + OR_HEADER_BYTES + 4 * k, (uint32_t)word_off);
+  if (flags & OR_FLAG_SUB) {
+    uint32_t M = B / S;
+    uint32_t* e = (uint32_t*)malloc((M > 1 ? M - 1 : 1) * sizeof(uint32_t));
+    if (!e) return OR_ERR_NOMEM;
+    oracle_sub_offsets(x + lo, hi - lo, len, S, M, e);
+    uint8_t* at = (uint8_t*)oracle_sub_entries(out, nb, B, flags, S, k);
+    for (uint32_t j = 0; j + 1 < M; ++j) put_u32(at + 4ull * j, e[j]);
+    free(e);
+  }
+  return OR_OK;
+}
+
+/*
+ * Compress x[0..n) with blocks of B symbols.  `given_len` may be NULL (build
+ * the code from x's histogram, Sec. 2) or a 256-entry length table that must
+ * be a prefix code covering every symbol present in x.  flags: bit 0 writes
+ * the block-offset index, bit 1 the sub-block offsets of every S symbols
+ * (R14; S is ignored without bit 1).  On OR_ERR_CAPACITY, *out_len holds the
+ * size needed.
+ */
+int oracle_compress(const uint8_t* x, uint64_t n, uint32_t B, const uint8_t* given_len,
+                    uint32_t flags, uint32_t S, uint8_t* out, uint64_t cap, uint64_t* out_len) {
+  uint8_t len[256];
+  uint64_t code[256];
+  *out_len = 0;
+  if (B == 0 || B > OR_MAX_BLOCK || n > 0xFFFFFFFFull || !oracle_layout_ok(flags, B, S))
+    return OR_ERR_ARG;
+  int st = oracle_stream_code(x, n, given_len, len, code);
+  if (st != OR_OK) return st;
 
   uint64_t size;
-  int st = oracle_stream_size(x, n, B, len, flags, &size);
+  st = oracle_stream_size(x, n, B, len, flags, S, &size);
   if (st != OR_OK) return st;
   *out_len = size;
   if (size > cap) return OR_ERR_CAPACITY;
 
   uint64_t nb = ceil_div(n, B);
   memset(out, 0, size);
-  memcpy(out, "HZB1", 4);
-  put_u32(out + 4, flags);
-  put_u64(out + 8, n);
-  put_u32(out + 16, B);
-  put_u32(out + 20, (uint32_t)nb);
-  memcpy(out + 24, len, 256);
-  uint64_t index_at = OR_HEADER_BYTES;
-  uint64_t blocks_at = index_at + ((flags & OR_FLAG_INDEX) ? 4 * nb : 0);
-
+  oracle_write_header(out, n, B, (uint32_t)nb, flags, S, len);
   uint64_t word_off = 0;
-  uint32_t* rec = NULL;
-  uint64_t rec_cap = 0;
   for (uint64_t k = 0; k < nb; ++k) {
     uint64_t lo = k * B, hi = lo + B < n ? lo + B : n;
-    uint64_t need = 1 + ceil_div(oracle_block_bits(x + lo, hi - lo, len), 32);
-    if (need > rec_cap) {
-      free(rec);
-      rec = (uint32_t*)malloc(need * sizeof(uint32_t));
-      if (!rec) return OR_ERR_NOMEM;
-      rec_cap = need;
-    }
-    uint64_t got = oracle_encode_block(x + lo, hi - lo, len, code, rec, rec_cap);
-    if (flags & OR_FLAG_INDEX) put_u32(out + index_at + 4 * k, (uint32_t)word_off);
-    for (uint64_t w = 0; w < got; ++w) put_u32(out + blocks_at + 4 * (word_off + w), rec[w]);
-    word_off += got;
+    st = oracle_write_block(out, x, n, B, (uint32_t)nb, flags, S, len, code, k, word_off);
+    if (st != OR_OK) return st;
+    word_off += 1 + ceil_div(oracle_block_bits(x + lo, hi - lo, len), 32);
   }
-  free(rec);
   return OR_OK;
 }
 
 /* ----------------------------------------------------- Sec. 2.1: decoding */
 
-/* Parse and check the container header. */
+/* Parse and check the container header; *S receives the sub-block size (0
+ * without flags bit 1). */
 int oracle_parse_header(const uint8_t* s, uint64_t s_len, uint64_t* n, uint32_t* flags,
-                        uint32_t* B, uint32_t* nb, uint8_t* len) {
+                        uint32_t* B, uint32_t* nb, uint32_t* S, uint8_t* len) {
+  *S = 0;
   if (s_len < OR_HEADER_BYTES || memcmp(s, "HZB1", 4) != 0) return OR_ERR_CORRUPT;
   *flags = get_u32(s + 4);
   *n = get_u64(s + 8);
   *B = get_u32(s + 16);
   *nb = get_u32(s + 20);
   memcpy(len, s + 24, 256);
-  if (*flags & ~OR_FLAG_INDEX) return OR_ERR_CORRUPT;
+  if (*flags & ~(OR_FLAG_INDEX | OR_FLAG_SUB)) return OR_ERR_CORRUPT;
   if (*B == 0 || *B > OR_MAX_BLOCK || *n > 0xFFFFFFFFull) return OR_ERR_CORRUPT;
   if ((uint64_t)*nb != ceil_div(*n, *B)) return OR_ERR_CORRUPT;
+  if (*flags & OR_FLAG_SUB) {
+    uint64_t at = OR_HEADER_BYTES + ((*flags & OR_FLAG_INDEX) ? 4ull * *nb : 0);
+    if (at + 4 > s_len) return OR_ERR_CORRUPT;
+    *S = get_u32(s + at);
+  }
+  if (!oracle_layout_ok(*flags, *B, *S)) return OR_ERR_CORRUPT;
   if (!kraft_ok(len)) return OR_ERR_CORRUPT;
   int present = 0;
   for (int s2 = 0; s2 < 256; ++s2) present |= len[s2] != 0;
@@ -401,84 +504,122 @@ int oracle_parse_header(const uint8_t* s, uint64_t s_len, uint64_t* n, uint32_t*
   return OR_OK;
 }
 
-/*
- * Decompress a stream.  Blocks are located by walking the length delimiters
- * (Sec. 2.1: the offset table is built from them); when the stream carries
- * the index, every entry must agree with that walk.  Each symbol is found one
- * bit at a time: after reading l bits as the integer v, a code of length l
- * matches when first[l] <= v < first[l] + count[l] (canonical codes occupy a
- * contiguous range at each length).  Each block must use exactly its
- * delimiter's bit count, its padding must be zero and the stream must end with
- * the last record.  *n_out receives n (also on OR_ERR_CAPACITY).
- */
-int oracle_decompress(const uint8_t* s, uint64_t s_len, uint8_t* out, uint64_t cap,
-                      uint64_t* n_out) {
-  uint64_t n;
-  uint32_t flags, B, nb;
-  uint8_t len[256];
-  *n_out = 0;
-  int st = oracle_parse_header(s, s_len, &n, &flags, &B, &nb, len);
-  if (st != OR_OK) return st;
-  *n_out = n;
-  if (n > cap) return OR_ERR_CAPACITY;
-
+/* Per length: the first canonical code value, how many codes, and the
+ * symbols in (length, symbol) order (canonical codes of one length are
+ * consecutive integers, R2). */
+void oracle_decode_tables(const uint8_t* len, oracle_dec_tables* t) {
   uint64_t code[256];
   oracle_canonical_codes(len, code);
-  /* per length: first code value, how many codes, and the symbols in order */
-  uint64_t first[OR_MAX_LEN + 1];
-  uint64_t count[OR_MAX_LEN + 1];
-  int sorted[256];
-  int start[OR_MAX_LEN + 1];
   int m = 0;
-  for (int l = 0; l <= OR_MAX_LEN; ++l) { first[l] = 0; count[l] = 0; start[l] = 0; }
+  for (int l = 0; l <= OR_MAX_LEN; ++l) { t->first[l] = 0; t->count[l] = 0; t->start[l] = 0; }
   for (int l = 1; l <= OR_MAX_LEN; ++l) {
-    start[l] = m;
+    t->start[l] = m;
     for (int sym = 0; sym < 256; ++sym) {
       if (len[sym] != l) continue;
-      if (count[l] == 0) first[l] = code[sym];
-      count[l] += 1;
-      sorted[m++] = sym;
+      if (t->count[l] == 0) t->first[l] = code[sym];
+      t->count[l] += 1;
+      t->sorted[m++] = sym;
     }
   }
+}
 
-  uint64_t index_at = OR_HEADER_BYTES;
-  uint64_t blocks_at = index_at + ((flags & OR_FLAG_INDEX) ? 4 * (uint64_t)nb : 0);
+/*
+ * Walk the length delimiters (Sec. 2.1: the offset table is built from them):
+ * record k starts 1 + ceil(bits/32) words after record k - 1.  rec_at[k]
+ * receives record k's byte offset in the stream.  When the stream carries the
+ * index, every entry must agree with the walk; every record must fit the
+ * stream and the stream must end with the last record.
+ */
+int oracle_locate_records(const uint8_t* s, uint64_t s_len, uint32_t flags, uint32_t B,
+                          uint32_t nb, uint32_t S, uint64_t* rec_at) {
+  uint64_t blocks_at = oracle_records_at(nb, B, flags, S);
   if (blocks_at > s_len) return OR_ERR_CORRUPT;
   uint64_t word_off = 0;
   for (uint64_t k = 0; k < nb; ++k) {
     if (flags & OR_FLAG_INDEX) {
-      if (get_u32(s + index_at + 4 * k) != word_off) return OR_ERR_CORRUPT;
+      if (get_u32(s + OR_HEADER_BYTES + 4 * k) != word_off) return OR_ERR_CORRUPT;
     }
-    uint64_t rec_at = blocks_at + 4 * word_off;
-    if (rec_at + 4 > s_len) return OR_ERR_CORRUPT;
-    uint64_t bits = get_u32(s + rec_at);
-    uint64_t nwords = ceil_div(bits, 32);
-    if (rec_at + 4 + 4 * nwords > s_len) return OR_ERR_CORRUPT;
-    const uint8_t* payload = s + rec_at + 4;
-    uint64_t lo = k * (uint64_t)B, hi = lo + B < n ? lo + B : n;
-    uint64_t p = 0;
-    for (uint64_t i = lo; i < hi; ++i) {
-      uint64_t v = 0;
-      int l = 0, found = -1;
-      while (found < 0) {
-        if (p >= bits || l >= OR_MAX_LEN) return OR_ERR_CORRUPT;
-        uint32_t word = get_u32(payload + 4 * (p / 32));
-        uint32_t bit = (word >> (31 - (p % 32))) & 1u;
-        v = (v << 1) | bit;
-        l += 1;
-        p += 1;
-        if (count[l] > 0 && v >= first[l] && v - first[l] < count[l])
-          found = sorted[start[l] + (int)(v - first[l])];
-      }
-      out[i] = (uint8_t)found;
-    }
-    if (p != bits) return OR_ERR_CORRUPT;
-    for (uint64_t q = bits; q < 32 * nwords; ++q) {
-      uint32_t word = get_u32(payload + 4 * (q / 32));
-      if ((word >> (31 - (q % 32))) & 1u) return OR_ERR_CORRUPT;
-    }
+    uint64_t at = blocks_at + 4 * word_off;
+    if (at + 4 > s_len) return OR_ERR_CORRUPT;
+    uint64_t nwords = ceil_div(get_u32(s + at), 32);
+    if (at + 4 + 4 * nwords > s_len) return OR_ERR_CORRUPT;
+    rec_at[k] = at;
     word_off += 1 + nwords;
   }
   if (blocks_at + 4 * word_off != s_len) return OR_ERR_CORRUPT;
   return OR_OK;
+}
+
+/*
+ * Decode one record (located and bounds-checked by oracle_locate_records)
+ * into its `count` symbols.  Each symbol is found one bit at a time: after
+ * reading l bits as the integer v, a code of length l matches when
+ * first[l] <= v < first[l] + count[l].  The block must use exactly its
+ * delimiter's bit count and its padding must be zero.  With sub-block
+ * offsets (`sub`: the record's M - 1 little-endian entries, R14), the code of
+ * symbol j*S must start at entry j - 1, and entries past the block's last
+ * symbol must equal bits_k.
+ */
+int oracle_decode_block(const oracle_dec_tables* t, const uint8_t* rec, uint64_t count,
+                        const uint8_t* sub, uint32_t S, uint32_t M, uint8_t* out) {
+  uint64_t bits = get_u32(rec);
+  uint64_t nwords = ceil_div(bits, 32);
+  const uint8_t* payload = rec + 4;
+  uint64_t p = 0;
+  for (uint64_t i = 0; i < count; ++i) {
+    if (sub && i > 0 && i % S == 0 && get_u32(sub + 4 * (i / S - 1)) != p) return OR_ERR_CORRUPT;
+    uint64_t v = 0;
+    int l = 0, found = -1;
+    while (found < 0) {
+      if (p >= bits || l >= OR_MAX_LEN) return OR_ERR_CORRUPT;
+      uint32_t word = get_u32(payload + 4 * (p / 32));
+      uint32_t bit = (word >> (31 - (p % 32))) & 1u;
+      v = (v << 1) | bit;
+      l += 1;
+      p += 1;
+      if (t->count[l] > 0 && v >= t->first[l] && v - t->first[l] < t->count[l])
+        found = t->sorted[t->start[l] + (int)(v - t->first[l])];
+    }
+    out[i] = (uint8_t)found;
+  }
+  if (p != bits) return OR_ERR_CORRUPT;
+  if (sub) {
+    for (uint64_t j = 1; j < M; ++j)
+      if (j * S >= count && get_u32(sub + 4 * (j - 1)) != bits) return OR_ERR_CORRUPT;
+  }
+  for (uint64_t q = bits; q < 32 * nwords; ++q) {
+    uint32_t word = get_u32(payload + 4 * (q / 32));
+    if ((word >> (31 - (q % 32))) & 1u) return OR_ERR_CORRUPT;
+  }
+  return OR_OK;
+}
+
+/*
+ * Decompress a stream: check the header, locate the records, then decode
+ * every block (exactly B symbols, the last one n - (nb-1)*B).  *n_out
+ * receives n (also on OR_ERR_CAPACITY).
+ */
+int oracle_decompress(const uint8_t* s, uint64_t s_len, uint8_t* out, uint64_t cap,
+                      uint64_t* n_out) {
+  uint64_t n;
+  uint32_t flags, B, nb, S;
+  uint8_t len[256];
+  *n_out = 0;
+  int st = oracle_parse_header(s, s_len, &n, &flags, &B, &nb, &S, len);
+  if (st != OR_OK) return st;
+  *n_out = n;
+  if (n > cap) return OR_ERR_CAPACITY;
+  oracle_dec_tables t;
+  oracle_decode_tables(len, &t);
+  uint64_t* rec_at = (uint64_t*)malloc((nb ? nb : 1) * sizeof(uint64_t));
+  if (!rec_at) return OR_ERR_NOMEM;
+  st = oracle_locate_records(s, s_len, flags, B, nb, S, rec_at);
+  uint32_t M = (flags & OR_FLAG_SUB) ? B / S : 1;
+  for (uint64_t k = 0; k < nb && st == OR_OK; ++k) {
+    uint64_t lo = k * (uint64_t)B, hi = lo + B < n ? lo + B : n;
+    const uint8_t* sub = oracle_sub_entries(s, nb, B, flags, S, k);
+    st = oracle_decode_block(&t, s + rec_at[k], hi - lo, sub, S, M, out + lo);
+  }
+  free(rec_at);
+  return st;
 }

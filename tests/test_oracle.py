@@ -4,6 +4,7 @@ independent reader, and the overhead bounds stated in Sec. 2.1 of the paper."""
 import itertools
 import os
 import random
+import struct
 from fractions import Fraction
 
 import numpy as np
@@ -30,11 +31,11 @@ def _load_golden(name):
     return spec, fields
 
 
-@pytest.mark.parametrize("name", ["abracadabra_b3.txt", "ties_b4.txt"])
+@pytest.mark.parametrize("name", ["abracadabra_b3.txt", "ties_b4.txt", "sub_offsets_b64.txt"])
 def test_hand_derived_streams(name):
     spec, fields = _load_golden(name)
     x = np.frombuffer(spec["input_ascii"].encode(), dtype=np.uint8)
-    s = oracle.compress(x, int(spec["block_size"])).tobytes()
+    s = oracle.compress(x, int(spec["block_size"]), sub=int(spec.get("sub_block", 0))).tobytes()
     assert len(s) == int(spec["stream_length"])
     want = bytearray(len(s))
     for off, b in fields:
@@ -366,3 +367,96 @@ def test_corrupt_streams_are_rejected():
         with pytest.raises(oracle.OracleError) as e:
             oracle.decompress(b)
         assert e.value.status == oracle.ERR_CORRUPT
+
+
+# ------------------------------------------------------------ sub-block offsets (R14)
+@pytest.mark.parametrize("n,B,S", [(0, 64, 32), (1, 64, 32), (100, 64, 32), (4096, 4096, 2048),
+                                   (4097, 4096, 1024), (70_001, 65_536, 2048),
+                                   (10_000, 96, 32), (5000, 2048, 2048), (3000, 64, 64)])
+def test_sub_block_offsets_round_trip_and_invariants(n, B, S):
+    x = _zipf_bytes(n, 1.1, n + 3 * B + S)
+    s = oracle.compress(x, B, sub=S)
+    c = format_reader.read_container(s.tobytes())
+    assert c["flags"] == 3 and c["S"] == S and c["end"] == s.size
+    lengths = np.array(c["lengths"], dtype=np.int64)
+    M = B // S
+    for k, rec in enumerate(c["records"]):
+        blk = x[k * B:(k + 1) * B]
+        # entry j: the sum of the code lengths of the block's first j*S symbols
+        want = [int(lengths[blk[:j * S]].sum()) for j in range(1, M)]
+        assert c["sub"][k] == want
+        assert all(0 < e <= rec["bits"] for e in want)
+    # the records are those of the stream without the section
+    plain = format_reader.read_container(oracle.compress(x, B).tobytes())
+    assert [r["words"] for r in plain["records"]] == [r["words"] for r in c["records"]]
+    assert s.size == oracle.compress(x, B).size + 4 + 4 * c["nb"] * (M - 1)
+    assert np.array_equal(oracle.decompress(s), x)
+    if n <= 20_000:
+        assert format_reader.decode(s.tobytes()) == x.tobytes()
+
+
+def test_sub_block_layout_is_checked():
+    x = _zipf_bytes(1000, 1.1, 1)
+    for B, S in ((64, 48), (64, 16), (96, 64), (32, 64)):  # S not a multiple of 32 dividing B
+        with pytest.raises(oracle.OracleError):
+            oracle.compress(x, B, sub=S)
+    with pytest.raises(oracle.OracleError):  # bit 1 needs bit 0
+        oracle.compress(x, 64, index=False, sub=32)
+
+
+def test_corrupt_sub_block_offsets_are_rejected():
+    x = _zipf_bytes(9000, 1.2, 4)
+    s = oracle.compress(x, 1024, sub=256)
+    c = format_reader.read_container(s.tobytes())
+    sec = 280 + 4 * c["nb"]          # the section: S, then 3 entries per block
+    bad = []
+    b = s.copy(); b[sec] = 64; bad.append(b)                      # S that does not match
+    b = s.copy(); b[sec + 4] ^= 1; bad.append(b)                  # first entry off by one
+    last = sec + 4 + 4 * 3 * (c["nb"] - 1) + 8                    # the last block's last entry
+    b = s.copy(); b[last] ^= 2; bad.append(b)                     # past its end: must be bits_k
+    b = s.copy(); b[4] = 2; bad.append(b)                         # bit 1 without bit 0
+    for b in bad:
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.decompress(b)
+        assert e.value.status == oracle.ERR_CORRUPT
+        with pytest.raises((ValueError, struct.error)):  # the naive reader fails too
+            format_reader.decode(b.tobytes())
+
+
+# ------------------------------------------------------------ OpenMP driver
+@pytest.mark.parametrize("threads", [1, 3, 0])
+def test_openmp_driver_writes_the_oracle_stream(threads):
+    rng = np.random.default_rng(8)
+    cases = [(0, 4096, 0), (1, 1, 0), (17, 3, 0), (100_003, 1000, 0), (300_000, 65_536, 2048),
+             (50_000, 4096, 1024), (65_537, 65_536, 0)]
+    for n, B, S in cases:
+        x = _zipf_bytes(n, float(rng.uniform(0.7, 1.6)), n + B)
+        for index in (True, False):
+            if S and not index:
+                continue
+            want = oracle.compress(x, B, index=index, sub=S)
+            got = oracle.compress_omp(x, B, index=index, sub=S, threads=threads)
+            assert np.array_equal(got, want), (n, B, S, index)
+            assert np.array_equal(oracle.decompress_omp(want, threads=threads), x)
+    # a given code, as for the sequential form
+    lens = np.zeros(256, dtype=np.uint8)
+    lens[:62] = np.arange(1, 63)
+    lens[62:64] = 63
+    x = rng.integers(0, 64, size=5000, dtype=np.uint8)
+    assert np.array_equal(oracle.compress_omp(x, 37, lengths=lens, threads=threads),
+                          oracle.compress(x, 37, lengths=lens))
+    assert oracle.omp_threads(threads) == (threads if threads else oracle.omp_threads(0))
+
+
+def test_openmp_driver_rejects_what_the_oracle_rejects():
+    x = _zipf_bytes(5000, 1.1, 2)
+    s = oracle.compress(x, 512, sub=256)
+    for b in (s[:-4].copy(), np.concatenate([s, np.zeros(4, np.uint8)])):
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.decompress_omp(b)
+        assert e.value.status == oracle.ERR_CORRUPT
+    b = s.copy(); b[280 + 4 * 10 + 8] ^= 1
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress_omp(b)
+    with pytest.raises(oracle.OracleError):
+        oracle.compress_omp(x, 64, sub=48)
