@@ -177,7 +177,10 @@ hz_status hz_decompress_host(hz_ctx* ctx, const uint8_t* h_in, uint64_t in_len, 
  * any stream capture.  Every call shares the one array and clears what must
  * start at zero, so calls that overlap on the GPU (different streams or host
  * threads without ordering) race; order them.  Asynchronous on `stream`
- * otherwise.  HZ_ERR_CUDA if a launch or the set-up fails.
+ * otherwise.  HZ_ERR_CUDA if a launch or the set-up fails.  block_size 0
+ * takes the built-in size table (<= 64 KiB: 4 KiB, <= 32 MiB: 16 KiB, larger:
+ * 64 KiB), never a context's autotuned choice, so for the same input it can
+ * pick another block size than hz_compress with block_size 0.
  */
 hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32_t block_size,
                               uint8_t* d_out, uint64_t out_cap, uint64_t* d_out_len,

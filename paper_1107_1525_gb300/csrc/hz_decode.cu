@@ -95,6 +95,8 @@ size_t decode_smem_bytes(int threads) {
 }
 
 // ================================================================ launchers
+static PerDeviceSetup<2> g_decode_setup;
+
 cudaError_t launch_decode_setup(const DecodeArgs& a, DecTables* T, cudaStream_t s) {
   decode_setup_kernel<<<1, 256, 0, s>>>(a, T);
   return cudaGetLastError();
@@ -104,19 +106,19 @@ cudaError_t launch_decode_blocks(const DecodeArgs& a, const DecTables* T, int th
                                  cudaStream_t s) {
   if (threads != 128) threads = kFastThreads;
   const size_t smem = decode_smem_bytes(threads);
-  // the attribute, and the CTAs resident per SM for each width, once per process
-  static bool configured = false;
-  static int per_sm_of[2] = {0, 0};
-  if (!configured) {
-    cudaFuncSetAttribute(decode_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)decode_smem_bytes(kFastThreads));
-    configured = true;
-  }
-  int& per_sm = per_sm_of[threads == 128 ? 0 : 1];
-  if (per_sm < 1) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_fast_kernel, threads, smem);
-    if (per_sm < 1) per_sm = 1;
-  }
+  // the raised shared-memory limit and the CTAs resident per SM hold for the
+  // device that is current when they are set or queried: kept per device
+  int per_sm = 1;
+  const cudaError_t e = launch_setup_per_device(
+      g_decode_setup, threads == 128 ? 0 : 1, &per_sm, [&](int& out) {
+        cudaError_t r = cudaFuncSetAttribute(decode_fast_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)decode_smem_bytes(kFastThreads));
+        if (r == cudaSuccess)
+          r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, decode_fast_kernel, threads, smem);
+        return r;
+      });
+  if (e != cudaSuccess) return e;
   uint64_t grid = (uint64_t)num_sms * per_sm;
   // a block range shorter than the resident warps needs fewer CTAs (the
   // block count itself is only known on the device: an unbounded range keeps

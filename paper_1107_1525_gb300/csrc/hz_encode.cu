@@ -211,16 +211,21 @@ cudaError_t launch_encode_scan(const EncodeArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+static PerDeviceSetup<1> g_pack_setup;
+
 cudaError_t launch_encode_pack(const EncodeArgs& a, int num_sms, cudaStream_t s) {
-  static bool configured = false;
   const int smem = (int)sizeof(PackShared);
-  if (!configured) {
-    cudaFuncSetAttribute(encode_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    configured = true;
-  }
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_pack_kernel, kEncThreads, smem);
-  const uint64_t grid = (uint64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+  // the raised shared-memory limit and the CTAs per SM, once per device
+  int per_sm = 1;
+  const cudaError_t e = launch_setup_per_device(g_pack_setup, 0, &per_sm, [&](int& out) {
+    cudaError_t r =
+        cudaFuncSetAttribute(encode_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (r == cudaSuccess)
+      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, encode_pack_kernel, kEncThreads, smem);
+    return r;
+  });
+  if (e != cudaSuccess) return e;
+  const uint64_t grid = (uint64_t)num_sms * per_sm;
   const uint32_t nt = a.tile_end - a.tile_begin;
   if (nt == 0) return cudaSuccess;
   encode_pack_kernel<<<(unsigned)(grid < nt ? grid : nt), kEncThreads, smem, s>>>(a);

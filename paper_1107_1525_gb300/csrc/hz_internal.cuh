@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "hz.h"
 
 namespace hz {
@@ -126,6 +128,42 @@ __device__ __forceinline__ uint32_t fast_div(uint32_t x, const FastDiv& f) {
 
 __device__ __forceinline__ uint32_t fast_mod(uint32_t x, const FastDiv& f) {
   return x - fast_div(x, f) * f.d;
+}
+
+// Launch set-up that belongs to a device -- a kernel's raised dynamic
+// shared-memory limit and the CTAs of it that fit on one SM hold for the
+// device that is current when they are set or queried -- done once per device
+// and variant, under a lock, and the CTAs-per-SM figure kept.
+constexpr int kMaxDevices = 64;
+template <int NV>
+struct PerDeviceSetup {
+  std::mutex mu;
+  int per_sm[kMaxDevices][NV] = {};
+};
+
+// f(int& per_sm) sets the device's attributes and queries the occupancy;
+// *per_sm receives the cached figure (at least 1) on success.
+template <int NV, class F>
+cudaError_t launch_setup_per_device(PerDeviceSetup<NV>& p, int variant, int* per_sm, F&& f) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) {  // not cached: set up on every launch
+    int v = 0;
+    e = f(v);
+    *per_sm = v > 0 ? v : 1;
+    return e;
+  }
+  std::lock_guard<std::mutex> lock(p.mu);
+  int& v = p.per_sm[dev][variant];
+  if (v < 1) {
+    int got = 0;
+    e = f(got);
+    if (e != cudaSuccess) return e;
+    v = got > 0 ? got : 1;
+  }
+  *per_sm = v;
+  return cudaSuccess;
 }
 
 struct EncodeArgs {

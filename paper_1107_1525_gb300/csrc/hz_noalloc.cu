@@ -23,7 +23,6 @@ constexpr size_t kScratchBytes = kStateBytes + (size_t)kNoallocMaxTiles * sizeof
 // Every GPU that loads the library holds this array (about 1 MiB) until exit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};  // device address of the array, per device
 
@@ -74,10 +73,10 @@ extern "C" hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32
   const uint32_t B = block_size ? block_size : hz_batch_tuned_block_size(n);
   const uint32_t nb = (uint32_t)((n + B - 1) / B);
   const uint32_t ntiles = (uint32_t)((n + kEncTile - 1) / kEncTile);
-  // the previous call's counters and histogram are still in the array: clear them
-  if (cudaMemsetAsync(&st->tile_counter, 0,
-                      offsetof(DevState, codes) - offsetof(DevState, tile_counter), s) !=
-      cudaSuccess)
+  // the previous call's status word, counters and histogram are still in the
+  // array: clear them (the status word too, in case a launch of the previous
+  // call failed before its finish kernel could clear it)
+  if (cudaMemsetAsync(st, 0, offsetof(DevState, codes), s) != cudaSuccess)
     return HZ_ERR_CUDA;
   LenParam none;
   memset(&none, 0, sizeof(none));

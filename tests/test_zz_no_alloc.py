@@ -2,16 +2,16 @@
 memory (for example code running under a framework's caching allocator or a fixed
 memory reservation that a cudaMalloc would bypass).  Its scratch is a fixed device
 array inside the library.  These checks call it through the C ABI and compare its
-stream with hz_compress's for the same input -- byte for byte, the tolerance every
-stream test here uses -- on two calls in a row, so that whatever the first call left
-in the shared array cannot leak into the second.  This file is collected last."""
-import ctypes
-
+stream with hz_compress's and with the CPU oracle's for the same input -- byte for
+byte, the tolerance every stream test here uses -- on two calls in a row, so that
+whatever the first call left in the shared array cannot leak into the second.  This
+file is collected last."""
 import numpy as np
 import pytest
 import torch
 
 import datagen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -66,6 +66,41 @@ def test_noalloc_matches_hz_compress_on_two_calls_in_a_row(hz):
         got = _without_allocation(hz, x, B)
         assert got.numel() == want.numel()
         assert torch.equal(got, want)
+        assert np.array_equal(got.cpu().numpy(), oracle.compress(x.cpu().numpy(), B))
+
+
+def test_noalloc_allocates_no_device_memory(hz):
+    x = datagen.zipf_buffer(5 * MiB + 3, s=1.1, seed=23, device=DEV)
+    _without_allocation(hz, x, 16384)  # the first call on the device sets up the array
+    lib = hz.load_library()
+    n = x.numel()
+    cap = hz.hz_compress_bound(n, 16384)
+    out = torch.empty(cap, dtype=torch.uint8, device=DEV)
+    out_len = torch.zeros(1, dtype=torch.int64, device=DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    assert lib.hz_compress_noalloc(x.data_ptr(), n, 16384, out.data_ptr(), cap,
+                                   out_len.data_ptr(), status.data_ptr(),
+                                   torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    assert int(status.item()) == 0
+    got = out[: int(out_len.item())].cpu().numpy()
+    assert np.array_equal(got, oracle.compress(x.cpu().numpy(), 16384))
+
+
+def test_noalloc_empty_input_and_builtin_block_size(hz):
+    # n = 0: a header-only stream
+    assert np.array_equal(_without_allocation(hz, torch.empty(0, dtype=torch.uint8, device=DEV),
+                                              4096).cpu().numpy(),
+                          oracle.compress(np.zeros(0, dtype=np.uint8), 4096))
+    # block_size 0 takes the built-in size table: 16 KiB for a buffer of 3 MiB
+    x = datagen.zipf_buffer(3 * MiB + 5, s=0.9, seed=24, device=DEV)
+    got = _without_allocation(hz, x, 0)
+    assert int(np.frombuffer(got[16:20].cpu().numpy().tobytes(), dtype="<u4")[0]) == 16384
+    assert np.array_equal(got.cpu().numpy(), oracle.compress(x.cpu().numpy(), 16384))
 
 
 def test_noalloc_rejects_inputs_beyond_its_scratch(hz):
