@@ -8,12 +8,22 @@
  * paper leaves unspecified).  All integers little-endian:
  *   offset 0    "HZB1"
  *   offset 4    u32 flags      bit 0: block-offset index present
+ *                              bit 1: sub-block offsets present (needs bit 0)
  *   offset 8    u64 n          uncompressed bytes
  *   offset 16   u32 B          symbols (bytes) per block
  *   offset 20   u32 nb         ceil(n / B)
  *   offset 24   u8  len[256]   Huffman code length of each byte value (0 = absent)
  *   offset 280  u32 word_offset[nb]   only if flags bit 0; record k's position
- *               in 32-bit words from the first byte after the index
+ *               in 32-bit words from the first byte after the index sections
+ *   then, only if flags bit 1: u32 S (a multiple of 32 that divides B), and
+ *               for every block k the B/S - 1 words u32 sub_offset[k][j],
+ *               j = 1 .. B/S - 1: the payload bit at which the code of the
+ *               block's symbol j*S starts (bits_k when the block has fewer
+ *               than j*S + 1 symbols).  The same kind of table as the index,
+ *               one level down: it lets the S-symbol parts of one block be
+ *               decoded independently (an addition to the paper's format,
+ *               which Sec. 2.1 leaves at block granularity; the records are
+ *               unchanged).
  *   then nb block records back to back.  Record k = u32 bits_k (the payload
  *   length in bits: the "unencoded four byte integer" of Sec. 2.1), then
  *   ceil(bits_k / 32) payload words holding the canonical codes of block k's
@@ -96,6 +106,15 @@ void hz_destroy(hz_ctx* ctx);
  * bound then assumes 1-byte blocks.  Returns 0 for n >= 2^32.
  */
 uint64_t hz_compress_bound(uint64_t n, uint32_t block_size);
+
+/*
+ * The same bound for the streams hz_compress writes on `ctx` with its current
+ * options: block_size 0 resolves to the context's choice, and with
+ * HZ_OPT_SUB_BLOCK = S (when S divides the block size) the bound includes the
+ * 4 + 4 * nb * (B/S - 1) bytes of sub-block offsets.  0 for a NULL ctx or
+ * n >= 2^32.
+ */
+uint64_t hz_compress_bound_ctx(hz_ctx* ctx, uint64_t n, uint32_t block_size);
 
 /*
  * Sec. 2 ("counting the appearance of every distinct symbol", then the
@@ -199,6 +218,22 @@ hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32_t block_si
 #define HZ_OPT_BATCH_MAX_REQS 7  /* most requests in one device batch when queued
                                     submissions merge (default 4096; a larger
                                     single submission still goes alone) */
+#define HZ_OPT_SUB_BLOCK 8    /* S > 0: hz_compress (and hz_compress_host) write the
+                                 sub-block offsets of every S symbols (flags bit 1)
+                                 when S divides the block size and the index is on;
+                                 S a multiple of 32.  0 (default): the paper's layout
+                                 with the block index only.  Decoders accept either. */
+#define HZ_OPT_SPIN_LIMIT 9   /* polls the encoder's look-back scan makes while waiting
+                                 for a predecessor before it records HZ_ERR_TIMEOUT and
+                                 returns (1 .. 2^24, default 2^20; each poll sleeps
+                                 about 64 ns) */
+#define HZ_OPT_INJECT_SCAN_STALL 10  /* host-side fault injection for tests: 1 = the
+                                 next hz_compress hands its scan CTAs tickets from 1
+                                 instead of 0, so the first one waits for a
+                                 predecessor that never publishes and its bounded wait
+                                 runs out; hz_sync then returns HZ_ERR_TIMEOUT.  One
+                                 shot: cleared when used.  Nothing on the device is
+                                 changed; the context stays usable. */
 
 /* Set an option; HZ_ERR_ARG for an unknown key or value. */
 hz_status hz_set_option(hz_ctx* ctx, int key, int64_t value);

@@ -59,6 +59,9 @@ struct hz_ctx {
   cudaEvent_t e_start = nullptr, e_in[kPipeGroups] = {}, e_dec[kPipeGroups] = {};
   // options
   int opt_index = 1;
+  uint32_t opt_sub = 0;  // symbols per sub-block for the sub-block offsets, 0 = none
+  uint32_t opt_spin_limit = kSpinLimit;
+  bool inject_scan_stall = false;  // one shot: the next scan's tickets start at 1
   int opt_profile = 0;
   int opt_lut_bits = 12;
   int opt_dec_threads = 256;
@@ -240,6 +243,17 @@ uint64_t hz_compress_bound(uint64_t n, uint32_t block_size) {
   return kHeaderBytes + 4 * nb + 12 * nb + 4 * ((n + 3) / 4);
 }
 
+uint64_t hz_compress_bound_ctx(hz_ctx* c, uint64_t n, uint32_t block_size) {
+  if (!c || n > 0xFFFFFFFFull) return 0;
+  const uint32_t B = block_size ? block_size : autotuned_block(c, n);
+  uint64_t bound = hz_compress_bound(n, B);
+  if (c->opt_index && c->opt_sub && sub_size_ok(B, c->opt_sub)) {
+    const uint64_t nb = (n + B - 1) / B;
+    bound += 4 + 4 * nb * (B / c->opt_sub - 1);
+  }
+  return bound;
+}
+
 hz_status hz_set_option(hz_ctx* c, int key, int64_t v) {
   if (!c) return HZ_ERR_ARG;
   switch (key) {
@@ -250,6 +264,18 @@ hz_status hz_set_option(hz_ctx* c, int key, int64_t v) {
     case HZ_OPT_PROFILE:
       if (v != 0 && v != 1) return HZ_ERR_ARG;
       c->opt_profile = (int)v;
+      return HZ_OK;
+    case HZ_OPT_SPIN_LIMIT:
+      if (v < 1 || v > (1 << 24)) return HZ_ERR_ARG;
+      c->opt_spin_limit = (uint32_t)v;
+      return HZ_OK;
+    case HZ_OPT_INJECT_SCAN_STALL:
+      if (v != 0 && v != 1) return HZ_ERR_ARG;
+      c->inject_scan_stall = v != 0;
+      return HZ_OK;
+    case HZ_OPT_SUB_BLOCK:
+      if (v != 0 && (v < 32 || v % 32 != 0 || v > (int64_t)kMaxBlock)) return HZ_ERR_ARG;
+      c->opt_sub = (uint32_t)v;
       return HZ_OK;
     case HZ_OPT_DECODE_LUT_BITS:
       if (v < kLutMinBits || v > kLutMaxBits) return HZ_ERR_ARG;
@@ -280,6 +306,9 @@ int64_t hz_get_option(hz_ctx* c, int key) {
   switch (key) {
     case HZ_OPT_INDEX: return c->opt_index;
     case HZ_OPT_PROFILE: return c->opt_profile;
+    case HZ_OPT_SUB_BLOCK: return c->opt_sub;
+    case HZ_OPT_SPIN_LIMIT: return c->opt_spin_limit;
+    case HZ_OPT_INJECT_SCAN_STALL: return c->inject_scan_stall ? 1 : 0;
     case HZ_OPT_DECODE_LUT_BITS: return c->opt_lut_bits;
     case HZ_OPT_DECODE_THREADS: return c->opt_dec_threads;
     case HZ_OPT_AUTOTUNE: return c->opt_autotune;
@@ -343,8 +372,9 @@ hz_status hz_sync(hz_ctx* c, void* stream) {
 
 // Enqueue histogram + code construction (Sec. 2) into the context state.
 static hz_status enqueue_codes(hz_ctx* c, const uint8_t* d_in, uint64_t n, const hz_codes* codes,
-                               uint32_t B, uint32_t nb, uint32_t flags, uint8_t* d_out,
-                               uint64_t out_cap, uint64_t* d_out_len, cudaStream_t s) {
+                               uint32_t B, uint32_t nb, uint32_t flags, uint32_t sub_S,
+                               uint8_t* d_out, uint64_t out_cap, uint64_t* d_out_len,
+                               cudaStream_t s) {
   // clear the ticket counters and the histogram (the status word is kept)
   if (cudaMemsetAsync(&c->d_state->tile_counter, 0,
                       offsetof(DevState, codes) - offsetof(DevState, tile_counter), s) !=
@@ -360,8 +390,8 @@ static hz_status enqueue_codes(hz_ctx* c, const uint8_t* d_in, uint64_t n, const
     if (st != HZ_OK) return st;
   }
   return launch(c, K_BUILD, s, [&] {
-    return launch_build_codes(c->d_state, codes ? 0 : 1, given, n, B, nb, flags, d_out, out_cap,
-                              d_out_len, s);
+    return launch_build_codes(c->d_state, codes ? 0 : 1, given, n, B, nb, flags, sub_S, d_out,
+                              out_cap, d_out_len, s);
   });
 }
 
@@ -397,7 +427,7 @@ hz_status hz_build_codes(hz_ctx* c, const uint8_t* d_in, uint64_t n, hz_codes* c
   if (!c || !codes_out || n > 0xFFFFFFFFull || (n && !d_in)) return HZ_ERR_ARG;
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
-  hz_status st = enqueue_codes(c, d_in, n, nullptr, 1, 0, 0, nullptr, 0, nullptr, s);
+  hz_status st = enqueue_codes(c, d_in, n, nullptr, 1, 0, 0, 0, nullptr, 0, nullptr, s);
   if (st != HZ_OK) return st;
   if (cudaMemcpyAsync(c->h_codes->len, c->d_state->codes.len, 256, cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
@@ -433,6 +463,13 @@ static hz_status encode_setup(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32
   a->B = B;
   a->nb = (uint32_t)((n + B - 1) / B);
   a->flags = c->opt_index ? kFlagIndex : 0;
+  // sub-block offsets when asked for and S suits B (they need the index)
+  const bool sub = c->opt_index && c->opt_sub && sub_size_ok(B, c->opt_sub);
+  if (sub) a->flags |= kFlagSub;
+  a->sub_S = sub ? c->opt_sub : 0;
+  a->sub_M = sub ? B / c->opt_sub : 1;
+  a->fdS = make_fastdiv(sub ? c->opt_sub : 1);
+  a->spin_limit = c->opt_spin_limit;
   a->out = d_out;
   a->out_cap = out_cap;
   a->out_len = d_out_len;
@@ -458,8 +495,15 @@ hz_status hz_compress(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32_t block
   EncodeArgs a;
   hz_status st = encode_setup(c, d_in, n, B, d_out, out_cap, d_out_len, &a);
   if (st != HZ_OK) return st;
-  st = enqueue_codes(c, d_in, n, codes, B, a.nb, a.flags, d_out, out_cap, d_out_len, s);
+  st = enqueue_codes(c, d_in, n, codes, B, a.nb, a.flags, a.sub_S, d_out, out_cap, d_out_len, s);
   if (st != HZ_OK || n == 0) return st;
+  if (c->inject_scan_stall) {
+    // host-side fault injection: no scan CTA gets ticket 0, so the first one
+    // looks back for a predecessor that never publishes, until its bounded
+    // wait runs out (HZ_ERR_TIMEOUT)
+    c->inject_scan_stall = false;
+    if (cudaMemsetAsync(&c->d_state->tile_counter, 1, 1, s) != cudaSuccess) return HZ_ERR_CUDA;
+  }
   st = launch(c, K_ENC_SUMMARY, s, [&] { return launch_encode_summary(a, c->num_sms, s); });
   if (st == HZ_OK) st = launch(c, K_ENC_SCAN, s, [&] { return launch_encode_scan(a, s); });
   if (st == HZ_OK) st = launch(c, K_ENC_PACK, s, [&] { return launch_encode_pack(a, c->num_sms, s); });
@@ -565,10 +609,18 @@ static hz_status decompress_host_pipelined(hz_ctx* c, const uint8_t* h_in, uint6
   memcpy(&n, h_in + 8, 8);
   memcpy(&B, h_in + 16, 4);
   memcpy(&nb, h_in + 20, 4);
-  if (memcmp(h_in, "HZB1", 4) != 0 || !(flags & kFlagIndex) || B == 0 || B > 65536 ||
-      nb < (uint32_t)kPipeGroups || (uint64_t)nb != (n + B - 1) / B || n > out_cap)
+  if (memcmp(h_in, "HZB1", 4) != 0 || !(flags & kFlagIndex) || (flags & ~(kFlagIndex | kFlagSub)) ||
+      B == 0 || nb < (uint32_t)kPipeGroups || (uint64_t)nb != (n + B - 1) / B || n > out_cap)
     return HZ_PENDING;
-  const uint64_t blocks_at = kHeaderBytes + 4ull * nb;
+  uint32_t S = 0;
+  if (flags & kFlagSub) {
+    if (kHeaderBytes + 4ull * nb + 4 > in_len) return HZ_PENDING;
+    memcpy(&S, h_in + kHeaderBytes + 4ull * nb, 4);
+    if (!sub_size_ok(B, S)) return HZ_PENDING;
+  } else if (B > 65536) {
+    return HZ_PENDING;  // blocks for the CTA-per-block decoder: one launch
+  }
+  const uint64_t blocks_at = records_at(nb, B, flags, S);
   if (blocks_at > in_len) return HZ_PENDING;
   // group g covers blocks [kg[g], kg[g + 1]) and stream bytes [at[g], at[g + 1])
   uint32_t kg[kPipeGroups + 1];
@@ -656,7 +708,7 @@ static hz_status compress_host_pipelined(hz_ctx* c, const uint8_t* h_in, uint64_
                                          uint64_t* out_len, cudaStream_t s) {
   if (n < kPipeMinBytes || !c->s_in || !c->s_out) return HZ_PENDING;
   const uint32_t B = block_size ? block_size : autotuned_block(c, n);
-  const uint64_t bound = hz_compress_bound(n, B);
+  const uint64_t bound = hz_compress_bound_ctx(c, n, B);
   const uint64_t dcap = out_cap < bound ? out_cap : bound;
   hz_status st = grow((void**)&c->d_hin, &c->d_hin_cap, n);
   if (st == HZ_OK) st = grow((void**)&c->d_hout, &c->d_hout_cap, dcap ? dcap : 16);
@@ -686,8 +738,8 @@ static hz_status compress_host_pipelined(hz_ctx* c, const uint8_t* h_in, uint64_
   memset(&none, 0, sizeof(none));
   if (st == HZ_OK)
     st = launch(c, K_BUILD, s, [&] {
-      return launch_build_codes(c->d_state, 1, none, n, B, a.nb, a.flags, c->d_hout, dcap,
-                                c->d_len, s);
+      return launch_build_codes(c->d_state, 1, none, n, B, a.nb, a.flags, a.sub_S, c->d_hout,
+                                dcap, c->d_len, s);
     });
   if (st == HZ_OK)
     st = launch(c, K_ENC_SUMMARY, s, [&] { return launch_encode_summary(a, c->num_sms, s); });
@@ -711,7 +763,7 @@ static hz_status compress_host_pipelined(hz_ctx* c, const uint8_t* h_in, uint64_
   *out_len = *c->h_len;
   if (st != HZ_OK) return st;
   if (*out_len > out_cap) return HZ_ERR_CAPACITY;
-  const uint64_t rec_base = kHeaderBytes + ((a.flags & kFlagIndex) ? 4ull * a.nb : 0ull);
+  const uint64_t rec_base = records_at(a.nb, a.B, a.flags, a.sub_S);
   uint64_t wb[kPipeGroups + 1];
   wb[0] = 0;
   for (int gi = 1; gi < kPipeGroups; ++gi) wb[gi] = c->h_len[gi];
@@ -747,7 +799,7 @@ hz_status hz_compress_host(hz_ctx* c, const uint8_t* h_in, uint64_t n, uint32_t 
   cudaStream_t s = (cudaStream_t)stream;
   hz_status st = compress_host_pipelined(c, h_in, n, block_size, h_out, out_cap, out_len, s);
   if (st != HZ_PENDING) return st;
-  const uint64_t bound = hz_compress_bound(n, block_size ? block_size : 1);
+  const uint64_t bound = hz_compress_bound_ctx(c, n, block_size);
   const uint64_t dcap = out_cap < bound ? out_cap : bound;
   st = grow((void**)&c->d_hin, &c->d_hin_cap, n ? n : 16);
   if (st == HZ_OK) st = grow((void**)&c->d_hout, &c->d_hout_cap, dcap ? dcap : 16);

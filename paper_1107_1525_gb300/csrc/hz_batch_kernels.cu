@@ -75,6 +75,10 @@ __device__ __forceinline__ EncodeArgs comp_args(const BatchComp& c) {
   a.fdB = c.fdB;
   a.tile_begin = 0;
   a.tile_end = c.ntiles;
+  a.sub_S = 0;  // batched streams carry no sub-block offsets
+  a.sub_M = 1;
+  a.fdS = FastDiv{1, 1, 0, 0};
+  a.spin_limit = kSpinLimit;  // (the batched scan runs in one CTA: no waits)
   return a;
 }
 
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(256) batch_build_kernel(BatchCtl* ctl, const B
   const LenParam none{};
   for (uint32_t i = blockIdx.x; i < ctl->ncomp; i += gridDim.x) {
     const BatchComp& c = comps[i];
-    build_codes_device(c.st, 1, none, c.n, c.B, c.nb, c.flags, c.dst, c.cap, c.out_len);
+    build_codes_device(c.st, 1, none, c.n, c.B, c.nb, c.flags, 0, c.dst, c.cap, c.out_len);
     __syncthreads();
   }
 }
@@ -255,7 +259,11 @@ __global__ void __launch_bounds__(1024) batch_dscan_kernel(BatchCtl* ctl, BatchD
     if (i < n) {
       BatchDecomp& d = decomps[i];
       const DecTables* T = d.T;
-      if (T->ok && T->nb) {
+      if (T->ok && T->nb && T->sub_M) {
+        // sub-block offsets: a unit is 8 warps of 32 sub-blocks, a lane each
+        d.per_warp = 0;
+        units = (T->units + 255) / 256;
+      } else if (T->ok && T->nb) {
         // a stream with few blocks gives every warp one block (latency); a
         // long one groups small blocks so that a table load serves 256 KiB
         const uint32_t per_warp =
@@ -304,12 +312,18 @@ __global__ void __launch_bounds__(kFastThreads, 3) batch_decode_kernel(BatchCtl*
     const DecTables* T = d.T;
     if (i != cur) {
       load_fast_tables(sh, T, threadIdx.x, kFastThreads);
+      if (threadIdx.x == 0) sh.args = decomp_args(d);
       cur = i;
       __syncthreads();
       mode = fast_mode(T, sh.c);
     }
     const DecodeArgs a = decomp_args(d);
     const uint32_t warp = threadIdx.x >> 5;
+    if (sh.sub_M) {  // uniform: 32 sub-blocks per warp
+      const uint32_t u0 = ((u - d.unit_base) * 8 + warp) * 32;
+      if (u0 < sh.units) decode_units_fast(u0, sh.units, mode);
+      continue;
+    }
     const uint32_t k0 = ((u - d.unit_base) * 8 + warp) * d.per_warp;
     for (uint32_t j = 0; j < d.per_warp; ++j) {
       const uint32_t k = k0 + j;

@@ -9,7 +9,8 @@ namespace hz {
 
 static __device__ void build_codes_device(DevState* st, int from_hist, const LenParam& given,
                                    uint64_t n, uint32_t B, uint32_t nb, uint32_t flags,
-                                   uint8_t* out, uint64_t out_cap, uint64_t* out_len) {
+                                   uint32_t sub_S, uint8_t* out, uint64_t out_cap,
+                                   uint64_t* out_len) {
   // weights fit 32 bits: every count and every sum of counts is at most n < 2^32
   __shared__ uint32_t s_freq[256];
   __shared__ uint32_t leaf_w[256];
@@ -153,13 +154,17 @@ static __device__ void build_codes_device(DevState* st, int from_hist, const Len
     return;
   }
   if (out == nullptr) return;
-  if (out_cap < kHeaderBytes) {
+  // an empty input's stream is the header and, with sub-block offsets, their S word
+  const uint64_t head = kHeaderBytes + ((flags & kFlagSub) ? 4ull * nb + 4 : 0ull);
+  if (out_cap < head) {
     if (t == 0) {
       set_error(st, HZ_ERR_CAPACITY, 0x101);
-      if (nb == 0) *out_len = kHeaderBytes;
+      if (nb == 0) *out_len = head;
     }
     return;
   }
+  if ((flags & kFlagSub) && t == 0)
+    *reinterpret_cast<uint32_t*>(out + kHeaderBytes + 4ull * nb) = sub_S;
   out[24 + t] = (uint8_t)myl;
   if (t < 24) {
     uint8_t b;
@@ -170,7 +175,7 @@ static __device__ void build_codes_device(DevState* st, int from_hist, const Len
     else b = (uint8_t)(nb >> (8 * (t - 20)));
     out[t] = b;
   }
-  if (nb == 0 && t == 0) *out_len = kHeaderBytes;
+  if (nb == 0 && t == 0) *out_len = head;
 }
 
 }  // namespace hz

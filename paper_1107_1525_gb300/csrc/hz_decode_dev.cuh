@@ -74,6 +74,9 @@ struct DecTables {
   uint32_t lut[1 << kLutMaxBits];
   uint32_t has_l2;              // the second-level table below is built
   uint16_t l2[kL2Entries];      // symbol | length << 8 of codes longer than W (0: none)
+  // sub-block offsets (flags bit 1): S symbols per sub-block, M = B / S per
+  // block (0 without them), units = nb * M
+  uint32_t sub_S, sub_M, units;
 };
 
 
@@ -131,9 +134,17 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   const uint32_t B = ld_u32_bytes(h + 16);
   const uint32_t nb = ld_u32_bytes(h + 20);
   bool ok = h[0] == 'H' && h[1] == 'Z' && h[2] == 'B' && h[3] == '1';
-  ok = ok && (flags & ~kFlagIndex) == 0 && B >= 1 && B <= kMaxBlock && n <= 0xFFFFFFFFull;
+  ok = ok && (flags & ~(kFlagIndex | kFlagSub)) == 0 && B >= 1 && B <= kMaxBlock &&
+       n <= 0xFFFFFFFFull;
   ok = ok && (uint64_t)nb == (n + B - 1) / (B ? B : 1);
-  const uint64_t blocks_at = kHeaderBytes + ((flags & kFlagIndex) ? 4ull * nb : 0ull);
+  // sub-block offsets: only with the index; S a multiple of 32 dividing B
+  uint32_t S = 0;
+  if (ok && (flags & kFlagSub)) {
+    ok = (flags & kFlagIndex) && kHeaderBytes + 4ull * nb + 4 <= a.in_len;
+    if (ok) S = ld_u32_bytes(h + kHeaderBytes + 4ull * nb);
+    ok = ok && sub_size_ok(B, S);
+  }
+  const uint64_t blocks_at = ok ? records_at(nb, B, flags, S) : 0ull;
   ok = ok && blocks_at <= a.in_len;
   const uint32_t l = h[24 + t];
   s_len[t] = l;
@@ -255,7 +266,9 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
   // Mode 0: every W-bit value starts a code of at most W bits.  The counting
   // pass's steps then take all the codes that end within cap bits: 10 when no
   // code is longer (so that three steps follow one buffer fill), else W.
-  const bool mode0 = s_complete && maxl <= (uint32_t)W && B <= kFastMaxB;
+  // (blocks over kFastMaxB only with sub-block offsets: their decoder takes
+  // mode 0; the CTA-per-block decoder does not)
+  const bool mode0 = s_complete && maxl <= (uint32_t)W && (B <= kFastMaxB || (flags & kFlagSub));
   const bool rep = mode0 && maxl <= 10 && W >= 10;
   const uint32_t cap = rep ? 10u : (uint32_t)W;
   for (uint32_t v = t * per; v < (t + 1) * per && v < nv; ++v) {
@@ -369,6 +382,9 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
     T->lut_bits = (uint32_t)W;
     T->fill_k = mode0 ? (rep ? (maxl <= 8 ? 4u : 3u) : 2u) : 0u;
     T->lut_rep = rep ? 1u : 0u;
+    T->sub_S = S;
+    T->sub_M = S ? B / S : 0u;
+    T->units = S ? nb * (B / S) : 0u;
     *a.out_len = n;
     if (!cap_ok) set_error(a.st, HZ_ERR_CAPACITY, 0x302);
   }
@@ -507,7 +523,12 @@ static_assert((1u << kLutMaxBits) + kL2Entries / 2 <= kFastLutWords, "table area
 struct FastShared {
   uint32_t lut[kFastLutWords];
   uint32_t has_l2, fill_k, lut_rep;
+  uint32_t sub_S, sub_M, units;  // sub-block offsets (sub_M = 0: none)
   CanonTables c;
+  // the launch's arguments (the stream being decoded), for the sub-block
+  // decoders: read from here they cost a shared-memory load, where a kernel
+  // parameter passed by reference to a separate function lives on the stack
+  DecodeArgs args;
 };
 
 // The fast decoders' shared state, one per CTA of any kernel that uses it, in
@@ -525,9 +546,13 @@ extern __shared__ __align__(16) uint8_t g_fast_smem[];
 static __device__ __forceinline__ FastShared& fast_sh() {
   return *reinterpret_cast<FastShared*>(g_fast_smem);
 }
-// this thread's payload ring
-static __device__ __forceinline__ uint32_t* fast_ring() {
-  return reinterpret_cast<uint32_t*>(g_fast_smem + kFastRingOffset) + threadIdx.x * kRingStride;
+// the dynamic shared memory as words, and this thread's payload ring as a
+// word index into it (32-bit shared-memory addressing, no generic pointer)
+static __device__ __forceinline__ uint32_t* fast_smem_words() {
+  return reinterpret_cast<uint32_t*>(g_fast_smem);
+}
+static __device__ __forceinline__ uint32_t fast_ring_word() {
+  return (uint32_t)(kFastRingOffset / 4) + threadIdx.x * kRingStride;
 }
 
 // The lookup tables of T into shared memory (all threads of the CTA).
@@ -550,6 +575,9 @@ static __device__ __forceinline__ void load_fast_tables(FastShared& sh, const De
     sh.has_l2 = has_l2;
     sh.fill_k = T->fill_k;
     sh.lut_rep = lut_rep;
+    sh.sub_S = T->sub_S;
+    sh.sub_M = T->sub_M;
+    sh.units = T->units;
   }
   load_canon(sh.c, T, tid, nt);
 }
@@ -564,6 +592,12 @@ static __device__ __forceinline__ void cp_async16(uint32_t smem_addr, const void
 }
 static __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// 32 bytes (8 words) to a 32-byte aligned global address in one request
+static __device__ __forceinline__ void st_global_v8(uint8_t* p, const uint32_t (&q)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(q[0]),
+               "r"(q[1]), "r"(q[2]), "r"(q[3]), "r"(q[4]), "r"(q[5]), "r"(q[6]), "r"(q[7])
+               : "memory");
 }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -581,7 +615,7 @@ struct RingWin {
   const uint8_t* abase;  // 16-byte aligned base of the payload's slots
   uint32_t full_slots;   // slots [0, full_slots) lie wholly inside the stream buffer
   uint32_t tail_bytes;   // bytes of slot full_slots inside the buffer
-  const uint32_t* ring;  // my ring (generic pointer into shared memory)
+  uint32_t ring_w;       // my ring: its first word's index in the dynamic shared memory
   uint32_t ring_s;       // my ring (shared-memory address)
   uint32_t off_w;        // payload word 0 = aligned word off_w
   uint32_t next_slot;    // next slot index (absolute) to request
@@ -589,15 +623,18 @@ struct RingWin {
   uint32_t nxt;          // that word, read from the ring one fill ahead
   uint32_t bh, bl, nb;
   uint32_t nacc;         // mode 0: nb = (32 * rw + nacc) mod 256
-  __device__ __forceinline__ void setup(const uint8_t* payload, const uint8_t* gend,
-                                        const uint32_t* my_ring) {
+  __device__ __forceinline__ void setup(const uint8_t* payload, const uint8_t* gend) {
     abase = reinterpret_cast<const uint8_t*>(((uintptr_t)payload) & ~(uintptr_t)15);
     off_w = (uint32_t)(payload - abase) >> 2;
     const uint64_t span = (uint64_t)(gend - abase);
     full_slots = (uint32_t)(span >> 5);
     tail_bytes = (uint32_t)(span & 31);
-    ring = my_ring;
-    ring_s = (uint32_t)__cvta_generic_to_shared(my_ring);
+    ring_w = fast_ring_word();
+    ring_s = (uint32_t)__cvta_generic_to_shared(fast_smem_words() + ring_w);
+  }
+  // word i (mod the ring) of my ring
+  __device__ __forceinline__ uint32_t ring(uint32_t i) const {
+    return fast_smem_words()[ring_w + i % kRingWords];
   }
   __device__ __forceinline__ void request(uint32_t h) {
     const uint32_t bytes = h < full_slots ? 32u : (h == full_slots ? tail_bytes : 0u);
@@ -621,13 +658,13 @@ struct RingWin {
     next_slot = h0 + 3;
     if (kLongSteps) cp_async_wait<0>();
     else cp_async_wait<1>();
-    const uint32_t w0 = ring[A % kRingWords], w1 = ring[(A + 1) % kRingWords];
+    const uint32_t w0 = ring(A), w1 = ring(A + 1);
     const uint32_t r = pos & 31u;
     bh = __funnelshift_l(w1, w0, r);
     bl = w1 << r;
     nb = 64u - r;
     rw = A + 2;
-    nxt = ring[rw % kRingWords];
+    nxt = ring(rw);
   }
   // Warp-uniform refill point, every kRefillSteps steps; slots up to rw / 8 + 3
   // are kept requested.  Steps of at most 12 bits read at most 6 words before
@@ -653,7 +690,7 @@ struct RingWin {
       bl |= lo;
       nb += 32u;
       ++rw;
-      nxt = ring[rw % kRingWords];
+      nxt = ring(rw);
     }
   }
   __device__ __forceinline__ uint32_t peek(uint32_t W) const { return bh >> (32u - W); }
@@ -676,14 +713,16 @@ struct RingWin {
   // the payload bit position of the next unread bit
   __device__ __forceinline__ uint32_t pos0() const { return 32u * (rw - off_w) - nb0(); }
   // a word into the buffer when it holds at most 32 bits (after it, more than 32)
+  // Without a branch: the shifts clamp at 32, so for n > 32 the high part
+  // adds nothing and the low part is selected away.
   __device__ __forceinline__ void fill0() {
     const uint32_t n = nb0();
-    if (n <= 32u) {
-      bh |= __funnelshift_rc(nxt, 0u, n);  // nxt >> n
-      bl |= __funnelshift_rc(0u, nxt, n);  // nxt << (32 - n)
-      ++rw;
-      nxt = ring[rw % kRingWords];
-    }
+    const bool take = n <= 32u;
+    bh |= __funnelshift_rc(nxt, 0u, n);                   // nxt >> n (0 for n >= 32)
+    const uint32_t lo = __funnelshift_rc(0u, nxt, n);     // nxt << (32 - n)
+    bl |= take ? lo : 0u;
+    rw += take ? 1u : 0u;
+    nxt = ring(rw);
   }
   __device__ __forceinline__ void take0(uint32_t h) {
     bh = __funnelshift_l(bl, bh, h);
@@ -838,7 +877,7 @@ __device__ __noinline__ void decode_block_warp(const DecodeArgs& a, uint32_t k) 
   g.p = reinterpret_cast<const uint32_t*>(payload);
   g.nw = nw;
   RingWin w;
-  w.setup(payload, a.in + a.in_len, fast_ring());
+  w.setup(payload, a.in + a.in_len);
   const uint32_t Lw = (nw + 31) / 32;
   const uint32_t L = Lw * 32;
   const uint32_t nsub = (bits + L - 1) / L;
@@ -1044,7 +1083,7 @@ __device__ __noinline__ void decode_block_warp0(const DecodeArgs& a, uint32_t k)
   g.p = reinterpret_cast<const uint32_t*>(payload);
   g.nw = nw;
   RingWin w;
-  w.setup(payload, a.in + a.in_len, fast_ring());
+  w.setup(payload, a.in + a.in_len);
   const uint32_t Lw = (nw + 31) / 32;
   const uint32_t L = Lw * 32;
   const uint32_t nsub = (bits + L - 1) / L;
@@ -1207,6 +1246,212 @@ static __device__ __forceinline__ void decode_block_fast(const DecodeArgs& a,
     else decode_block_warp0<2, 2, false>(a, k);
   } else if (mode == 1) decode_block_warp<1>(a, k);
   else decode_block_warp<2>(a, k);
+}
+
+// ================================================================ sub-block decoder
+// Streams with sub-block offsets (flags bit 1): the stored offsets give the
+// payload bit of the code of every S-th symbol of a block, so a lane decodes
+// the S symbols of one sub-block from a known bit straight into their place
+// in the output -- one pass over the payload, with no speculative counting,
+// no fix-up and no scan.  Unit u = k * M + j is symbols [j*S, min((j+1)*S,
+// cnt_k)) of block k (units past the last block's end hold no symbol); a warp
+// takes 32 consecutive units, lane l the unit u0 + l.
+struct SubRange {
+  const uint8_t* payload;  // the unit's record payload
+  uint32_t nw;             // the record's payload words
+  uint32_t start, end;     // payload bits [start, end) hold the unit's codes
+  uint32_t count;          // its symbols
+  uint64_t out_at;         // output index of its first symbol
+  bool ok;
+};
+
+// Unit u's range, checked: the record itself (read_record: index, delimiter,
+// padding), offsets in order and inside the record, at least one and at most
+// maxlen bits per symbol, the block's last unit ending at bits_k, and the
+// entries past the block's last symbol equal to bits_k (each entry is the
+// start of exactly one unit, so every entry gets checked).
+static __device__ __forceinline__ SubRange sub_range(const DecodeArgs& a, const CanonTables& c,
+                                                     uint32_t S, uint32_t M, uint32_t u) {
+  SubRange r;
+  const uint32_t k = u / M, j = u - k * M;
+  const RecInfo rec = read_record(a, c, k);
+  const uint32_t* e =
+      reinterpret_cast<const uint32_t*>(a.in + sub_entries_at(c.nb)) + (uint64_t)k * (M - 1);
+  const uint32_t lo = j * S;
+  r.payload = a.in + rec.rec + 4;
+  r.nw = rec.nw;
+  r.count = lo < rec.cnt_k ? min(S, rec.cnt_k - lo) : 0u;
+  r.start = j ? e[j - 1] : 0u;
+  r.end = j + 1 < M ? e[j] : rec.bits;
+  r.out_at = (uint64_t)k * c.B + lo;
+  bool ok = rec.ok && r.start <= r.end && r.end <= rec.bits;
+  if (r.count == 0) {
+    ok = ok && r.start == rec.bits;
+  } else {
+    ok = ok && r.end - r.start >= r.count &&
+         (uint64_t)(r.end - r.start) <= (uint64_t)r.count * c.maxlen;
+    if (lo + r.count == rec.cnt_k) ok = ok && r.end == rec.bits;
+  }
+  r.ok = ok;
+  return r;
+}
+
+// Mode 0 (see decode_block_warp0): one code per step from the mode-0 table,
+// a buffer fill every K2 steps, 16 symbols per 16-byte store.  Inlined into
+// the single-stream kernel (no call: its registers are the kernel's own), a
+// separate function in the batched one.
+template <int K2, bool kRep>
+__device__ __forceinline__ void decode_units0_body(uint32_t u0, uint32_t u_end) {
+  FastShared& sh = fast_sh();
+  const DecodeArgs& a = sh.args;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t sW = 32u - sh.c.W;
+  const uint32_t c2 = (lane & 7u) << 1;
+  const uint32_t u = u0 + lane;
+  SubRange r;
+  r.ok = true;
+  r.count = 0;
+  r.out_at = 0;
+  if (u < u_end) r = sub_range(a, sh.c, sh.sub_S, sh.sub_M, u);
+  bool bad = !r.ok;
+  uint32_t rem = r.ok ? r.count : 0u;
+  uint8_t* dst = a.out + r.out_at;
+  RingWin w;
+  // one code: its symbol (the high half's byte 1) and the buffer advanced
+  auto step = [&]() -> uint32_t {
+    const uint32_t h = lut0_hi(sh, lut0_at<kRep>(w.bh, sW, c2));
+    w.take0(h);
+    return h;
+  };
+  if (rem) {
+    w.setup(r.payload, a.in + a.in_len);
+    w.init0(r.start);
+    // bytes up to a 32-byte boundary, a refill point every 8 (a step reads at
+    // most 12 bits: 8 steps stay within the slots a refill awaits)
+    while (rem && (((uintptr_t)dst) & 31)) {
+      if ((((uintptr_t)dst) & 7) == 0) w.refill<false>();
+      w.fill0();
+      *dst++ = (uint8_t)(step() >> 8);
+      --rem;
+    }
+  }
+  // 32 symbols per 32-byte store (one whole sector per write request), a
+  // refill point every 16
+  while (__any_sync(0xFFFFFFFFu, rem >= 32)) {
+    if (rem >= 32) {
+      uint32_t q[8];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        w.refill<false>();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint32_t word = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            if ((4 * j + b) % K2 == 0) w.fill0();
+            const uint32_t h = step();
+            // byte b of the word <- the symbol (byte 1 of h)
+            word = __byte_perm(word, h, b == 0 ? 0x3215u : b == 1 ? 0x3250u : b == 2 ? 0x3510u : 0x5210u);
+          }
+          q[4 * half + j] = word;
+        }
+      }
+      st_global_v8(dst, q);
+      dst += 32;
+      rem -= 32;
+    }
+  }
+  if (rem) {
+    while (rem) {
+      if ((rem & 7) == 0) w.refill<false>();
+      w.fill0();
+      *dst++ = (uint8_t)(step() >> 8);
+      --rem;
+    }
+  }
+  if (r.ok && r.count) bad = w.pos0() != r.end;
+  cp_async_wait<0>();  // nothing of this warp's units may land in the ring after we leave
+  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x330);
+}
+
+template <int K2, bool kRep>
+__device__ __noinline__ void decode_units_warp0(uint32_t u0, uint32_t u_end) {
+  decode_units0_body<K2, kRep>(u0, u_end);
+}
+
+// Modes 1 and 2 (see decode_block_warp): one code per step from the general
+// table; longer codes through the second-level table or from memory.
+template <int kMode>
+__device__ __noinline__ void decode_units_warp(uint32_t u0, uint32_t u_end) {
+  FastShared& sh = fast_sh();
+  const DecodeArgs& a = sh.args;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t W = sh.c.W;
+  const uint32_t u = u0 + lane;
+  SubRange r;
+  r.ok = true;
+  r.count = 0;
+  r.out_at = 0;
+  r.payload = a.in;
+  r.nw = 0;
+  r.start = 0;
+  if (u < u_end) r = sub_range(a, sh.c, sh.sub_S, sh.sub_M, u);
+  bool bad = !r.ok;
+  uint32_t rem = r.ok ? r.count : 0u;
+  uint32_t pos = r.start;
+  uint8_t* dst = a.out + r.out_at;
+  GWin g;  // plain reader for codes longer than the table (mode 2)
+  g.p = reinterpret_cast<const uint32_t*>(r.payload);
+  g.nw = r.nw;
+  RingWin w;
+  if (rem) {
+    w.setup(r.payload, a.in + a.in_len);
+    w.template init<kMode == 1>(pos);
+    while (rem && (((uintptr_t)dst) & 15)) {
+      *dst++ = (uint8_t)ring_take<kMode>(sh, w, pos, W, g, bad);
+      --rem;
+    }
+  }
+  while (__any_sync(0xFFFFFFFFu, rem >= 16)) {
+    if (rem >= 16) {
+      w.template refill<kMode == 1>();
+      uint32_t q[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          w.fill();
+          word |= ring_step<kMode>(sh, w, pos, W, g, bad) << (8 * b);
+        }
+        q[j] = word;
+      }
+      *reinterpret_cast<uint4*>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
+      dst += 16;
+      rem -= 16;
+    }
+  }
+  if (rem) {
+    w.template refill<kMode == 1>();
+    while (rem) {
+      *dst++ = (uint8_t)ring_take<kMode>(sh, w, pos, W, g, bad);
+      --rem;
+    }
+  }
+  if (r.ok && r.count) bad |= pos != r.end;
+  cp_async_wait<0>();
+  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x331);
+}
+
+// Units [u0, u0 + 32) of the stream whose arguments are in fast_sh().args,
+// capped at u_end, in the stream's mode.
+static __device__ __forceinline__ void decode_units_fast(uint32_t u0, uint32_t u_end, int mode) {
+  if (mode == 0) {
+    if (fast_sh().fill_k == 4) decode_units_warp0<4, true>(u0, u_end);
+    else if (fast_sh().fill_k == 3) decode_units_warp0<3, true>(u0, u_end);
+    else decode_units_warp0<2, false>(u0, u_end);
+  } else if (mode == 1) decode_units_warp<1>(u0, u_end);
+  else decode_units_warp<2>(u0, u_end);
 }
 
 // ================================================================ generic kernel

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kScanThreads) encode_scan_kernel(EncodeArgs a)
           uint32_t f = ld_acquire(&st->scan_flags[idx]);
           uint32_t spins = 0;
           while (f == 0) {
-            if (++spins > kSpinLimit) {
+            if (++spins > a.spin_limit) {
               timed_out = true;
               break;
             }

@@ -222,7 +222,7 @@ static __device__ __forceinline__ void summary_tile(const EncodeArgs& a, uint32_
 // The stream size, from the state after the last tile, and the capacity check.
 static __device__ __forceinline__ void finish_stream(const EncodeArgs& a, const ScanState& s,
                                               bool aborted) {
-  const uint64_t rec_base = kHeaderBytes + ((a.flags & kFlagIndex) ? 4ull * a.nb : 0ull);
+  const uint64_t rec_base = records_at(a.nb, a.B, a.flags, a.sub_S);
   const uint64_t words = s.O + 1 + ceil32(s.b);
   const uint64_t size = rec_base + 4 * words;
   *a.out_len = size;
@@ -287,6 +287,27 @@ static __device__ void scan_tiles_cta(const EncodeArgs& a, Summary* s_warp /* [3
 }
 
 // =================================================================== pass 3
+// Sub-block offsets (flags bit 1).  Every sub-block boundary (symbol j*S of a
+// block, j >= 1) is the first symbol of some thread's 32-symbol run, since B
+// and S are multiples of 32; that thread knows the payload bit its run starts
+// at and writes the entry.
+static __device__ __forceinline__ void put_sub_entry(const EncodeArgs& a, uint32_t g,
+                                                     uint32_t bit) {
+  const uint32_t k = fast_div(g, a.fdB);
+  const uint32_t r = g - k * a.B;  // position in the block
+  if (r == 0 || fast_mod(r, a.fdS) != 0) return;
+  uint32_t* e = reinterpret_cast<uint32_t*>(a.out + sub_entries_at(a.nb));
+  e[(uint64_t)k * (a.sub_M - 1) + fast_div(r, a.fdS) - 1] = bit;
+}
+// The last block's entries past its last symbol hold its payload bit count.
+static __device__ __forceinline__ void put_sub_tail(const EncodeArgs& a, uint32_t bits) {
+  const uint32_t k = a.nb - 1;
+  const uint32_t cnt = (uint32_t)(a.n - (uint64_t)k * a.B);
+  uint32_t* e = reinterpret_cast<uint32_t*>(a.out + sub_entries_at(a.nb)) +
+                (uint64_t)k * (a.sub_M - 1);
+  for (uint32_t j = fast_div(cnt + a.sub_S - 1, a.fdS); j < a.sub_M; ++j) e[j - 1] = bits;
+}
+
 struct PackShared {
   EncodeArgs a;         // the launch arguments, read by the per-tile functions
   uint32_t entry[256];  // code << 6 | len, valid for codes of up to 26 bits
@@ -515,6 +536,7 @@ __device__ __noinline__ void pack_tile_single(PackShared& sh, uint32_t tile, con
     if (kKind == 2) pack_entries_wide(sh, x, lp, sh.stage + off, (p >> 5) - (b0 >> 5), p & 31u);
     else pack_entries<kKind == 0>(e, sh.stage + off, (p >> 5) - (b0 >> 5), p & 31u);
   }
+  if ((a.flags & kFlagSub) && g.my_cnt > 0) put_sub_entry(a, g.g0, b0 + ex);
   __syncthreads();
   // the last word belongs to the next tile when the record goes on mid-word
   const bool skip_last = !g.ends_record && (bend & 31u) != 0;
@@ -522,6 +544,7 @@ __device__ __noinline__ void pack_tile_single(PackShared& sh, uint32_t tile, con
            0xFFFFFFFFu);
   if (tid == 0) {
     if (g.ends_record) rec_words[O1] = bend;  // this tile holds the record's last symbol
+    if ((a.flags & kFlagSub) && g.hi == (uint32_t)a.n) put_sub_tail(a, bend);
     if (g.starts_record && (a.flags & kFlagIndex))
       reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[fast_div(g.lo, a.fdB)] = (uint32_t)O1;
   }
@@ -598,7 +621,9 @@ __device__ __noinline__ void pack_tile_chunked(PackShared& sh, uint32_t tile, co
       // last chunk of a record: its delimiter is now known
       if (myO >= w_first) st[myO - w_first] = myb + bits;
       else rec_words[myO] = myb + bits;
+      if ((a.flags & kFlagSub) && gend == (uint32_t)a.n) put_sub_tail(a, myb + bits);
     }
+    if (a.flags & kFlagSub) put_sub_entry(a, g.g0, myb);
     if (starts && (a.flags & kFlagIndex))
       reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[fast_div(g.g0, a.fdB)] = (uint32_t)myO;
   }
@@ -691,6 +716,8 @@ __device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, co
     uint64_t acc = 0;
     uint32_t next_start = first_start;
     uint32_t next_end = first_end;
+    // (sub-block offsets need B a multiple of 32: no record starts inside the run)
+    if ((a.flags & kFlagSub) && wlo == w_first && g.my_cnt > 0) put_sub_entry(a, g.g0, cur.b);
 #pragma unroll
     for (int i = 0; i < kEncSymPerThread; ++i) {
       if (i < g.my_cnt) {
@@ -736,6 +763,7 @@ __device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, co
           // last symbol of a record: its delimiter is now known
           if (cur.O >= wlo && cur.O < whi) sh.stage[cur.O - wlo] = cur.b;
           else if (cur.O < w_first && wlo == w_first) rec_words[cur.O] = cur.b;
+          if ((a.flags & kFlagSub) && wlo == w_first && next_end == n) put_sub_tail(a, cur.b);
           next_end = (uint32_t)min((uint64_t)next_end + B, (uint64_t)n);
         }
       }
@@ -769,8 +797,8 @@ static __device__ __forceinline__ void pack_load_tables(PackShared& sh, const En
 // Pack one tile of the buffer whose tables and arguments are in sh.
 static __device__ __forceinline__ void pack_one_tile(PackShared& sh, uint32_t tile, uint32_t maxlen) {
   const EncodeArgs& a = sh.a;
-  uint32_t* rec_words = reinterpret_cast<uint32_t*>(
-      a.out + kHeaderBytes + ((a.flags & kFlagIndex) ? 4ull * a.nb : 0ull));
+  uint32_t* rec_words =
+      reinterpret_cast<uint32_t*>(a.out + records_at(a.nb, a.B, a.flags, a.sub_S));
   const TileGeom g = tile_geom(tile, (uint32_t)a.n, a.fdB);
   const bool chunked_ok = a.fdB.d % kEncSymPerThread == 0;
   if (maxlen > 32) pack_tile_general<true>(sh, tile, g, rec_words);

@@ -16,6 +16,10 @@ constexpr uint32_t kHeaderBytes = 280;
 constexpr uint32_t kMaxBlock = 1u << 24;
 constexpr int kMaxLen = 64;
 constexpr uint32_t kFlagIndex = 1;
+// Sub-block offsets (flags bit 1, only with bit 0): after the index, u32 S and
+// then, per block, the payload bit offsets of its symbols S, 2S, ..., B - S.
+// S is a multiple of 32 dividing B.
+constexpr uint32_t kFlagSub = 2;
 // Bounded spin waits: a wait that runs out records HZ_ERR_TIMEOUT and the
 // kernel gives up the work item instead of hanging the GPU.
 constexpr uint32_t kSpinLimit = 1u << 20;
@@ -86,6 +90,23 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
 }
 
 __device__ __forceinline__ uint32_t ceil32(uint64_t bits) { return (uint32_t)((bits + 31) >> 5); }
+
+// Stream layout: bytes before the first record (header, index, sub-block
+// section), and where the sub-block entries start.
+__host__ __device__ __forceinline__ uint64_t records_at(uint64_t nb, uint32_t B, uint32_t flags,
+                                                        uint32_t S) {
+  uint64_t at = kHeaderBytes;
+  if (flags & kFlagIndex) at += 4 * nb;
+  if (flags & kFlagSub) at += 4 + 4 * nb * (uint64_t)(B / S - 1);
+  return at;
+}
+__host__ __device__ __forceinline__ uint64_t sub_entries_at(uint64_t nb) {
+  return kHeaderBytes + 4 * nb + 4;
+}
+// A sub-block size S suits blocks of B symbols.
+__host__ __device__ __forceinline__ bool sub_size_ok(uint32_t B, uint32_t S) {
+  return S >= 32 && S % 32 == 0 && B % S == 0;
+}
 
 // ------------------------------------------------------------ launchers
 // Kernel ids for the profile log.
@@ -180,6 +201,10 @@ struct EncodeArgs {
   uint32_t ntiles;
   FastDiv fdB;              // division by B
   uint32_t tile_begin, tile_end;  // tiles the single-buffer packing launch packs
+  // sub-block offsets (flags bit 1): S symbols per sub-block, M = B / S per block
+  uint32_t sub_S, sub_M;
+  FastDiv fdS;              // division by S (S = 1 without bit 1)
+  uint32_t spin_limit;      // polls of the scan's look-back before it gives up
 };
 
 struct DecodeArgs {
@@ -206,8 +231,8 @@ struct LenParam {
   uint8_t len[256];
 };
 cudaError_t launch_build_codes(DevState* st, int from_hist, const LenParam& given, uint64_t n,
-                               uint32_t B, uint32_t nb, uint32_t flags, uint8_t* out,
-                               uint64_t out_cap, uint64_t* out_len, cudaStream_t s);
+                               uint32_t B, uint32_t nb, uint32_t flags, uint32_t sub_S,
+                               uint8_t* out, uint64_t out_cap, uint64_t* out_len, cudaStream_t s);
 // The encoder's three launches: length-sum pass, scan, packing.
 cudaError_t launch_encode_summary(const EncodeArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_encode_scan(const EncodeArgs& a, cudaStream_t s);

@@ -81,7 +81,7 @@ extern "C" hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32
   LenParam none;
   memset(&none, 0, sizeof(none));
   if (n > 0 && launch_histogram(d_in, n, st, num_sms, s) != cudaSuccess) return HZ_ERR_CUDA;
-  if (launch_build_codes(st, 1, none, n, B, nb, kFlagIndex, d_out, out_cap, d_out_len, s) !=
+  if (launch_build_codes(st, 1, none, n, B, nb, kFlagIndex, 0, d_out, out_cap, d_out_len, s) !=
       cudaSuccess)
     return HZ_ERR_CUDA;
   if (n > 0) {
@@ -100,6 +100,10 @@ extern "C" hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32
     a.tile_begin = 0;
     a.tile_end = ntiles;
     a.fdB = make_fastdiv(B);
+    a.sub_S = 0;
+    a.sub_M = 1;
+    a.fdS = make_fastdiv(1);
+    a.spin_limit = kSpinLimit;
     if (launch_encode_summary(a, num_sms, s) != cudaSuccess ||
         launch_encode_scan(a, s) != cudaSuccess || launch_encode_pack(a, num_sms, s) != cudaSuccess)
       return HZ_ERR_CUDA;

@@ -70,7 +70,12 @@ extern "C" hz_status hz_autotune(hz_ctx* c, const uint8_t* d_sample, uint64_t n,
   cudaSetDevice(hz_ctx_device(c));
   cudaStream_t s = (cudaStream_t)stream;
   const uint64_t m_max = n < kClassSize[3] ? n : kClassSize[3];
-  const uint64_t cap = hz_compress_bound(m_max, 4096);
+  // room for the largest trial stream (with the context's options, e.g. sub-block offsets)
+  uint64_t cap = 0;
+  for (uint32_t B : kCandB) {
+    const uint64_t b = hz_compress_bound_ctx(c, m_max, B);
+    cap = b > cap ? b : cap;
+  }
   uint8_t *d_out = nullptr, *d_dec = nullptr;
   uint64_t* d_len = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -24,11 +24,13 @@ STATUS_NAMES = {0: "HZ_OK", 1: "HZ_PENDING", -1: "HZ_ERR_ARG", -2: "HZ_ERR_CAPAC
 HEADER_BYTES = 280
 HZ_OPT_INDEX, HZ_OPT_PROFILE, HZ_OPT_DECODE_LUT_BITS = 1, 2, 3
 HZ_OPT_DECODE_THREADS, HZ_OPT_AUTOTUNE, HZ_OPT_BATCH_PLAIN = 4, 5, 6
-HZ_OPT_BATCH_MAX_REQS = 7
+HZ_OPT_BATCH_MAX_REQS, HZ_OPT_SUB_BLOCK = 7, 8
+HZ_OPT_SPIN_LIMIT, HZ_OPT_INJECT_SCAN_STALL = 9, 10
 HZ_OP_COMPRESS, HZ_OP_DECOMPRESS = 0, 1
 
 # the C symbols include/hz.h declares (checked by the test suite)
-EXPORTS = ("hz_create", "hz_destroy", "hz_compress_bound", "hz_build_codes", "hz_compress",
+EXPORTS = ("hz_create", "hz_destroy", "hz_compress_bound", "hz_compress_bound_ctx",
+           "hz_build_codes", "hz_compress",
            "hz_decompress", "hz_sync", "hz_compress_host", "hz_decompress_host",
            "hz_set_option", "hz_get_option", "hz_launch_count", "hz_profile_read",
            "hz_kernel_name", "hz_submit", "hz_poll", "hz_compress_noalloc", "hz_autotune",
@@ -76,6 +78,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "hz_create": (i32, [ctypes.POINTER(vp), ctypes.c_int, u64]),
         "hz_destroy": (None, [vp]),
         "hz_compress_bound": (u64, [u64, u32]),
+        "hz_compress_bound_ctx": (u64, [vp, u64, u32]),
         "hz_build_codes": (i32, [vp, vp, u64, ctypes.POINTER(HzCodes), vp]),
         "hz_compress": (i32, [vp, vp, u64, u32, ctypes.POINTER(HzCodes), vp, u64, vp, vp]),
         "hz_decompress": (i32, [vp, vp, u64, vp, u64, vp, vp]),
@@ -179,6 +182,10 @@ def hz_destroy(ctx: Context):
 
 def hz_compress_bound(n: int, block_size: int) -> int:
     return int(load_library().hz_compress_bound(n, block_size))
+
+
+def hz_compress_bound_ctx(ctx: Context, n: int, block_size: int) -> int:
+    return int(ctx._lib.hz_compress_bound_ctx(ctx.handle, n, block_size))
 
 
 def hz_build_codes(ctx: Context, d_in, n: int, stream=None):
@@ -290,7 +297,7 @@ def compress(x, block_size: int = 0, ctx: Context | None = None, codes=None, str
     import torch
     ctx = ctx or default_context(x.device.index or 0)
     n = x.numel()
-    cap = hz_compress_bound(n, block_size or 1) if codes is None else 280 + 16 * n + 4096
+    cap = hz_compress_bound_ctx(ctx, n, block_size) if codes is None else 280 + 16 * n + 4096
     out = torch.empty(cap, dtype=torch.uint8, device=x.device)
     out_len = torch.zeros(1, dtype=torch.int64, device=x.device)
     hz_compress(ctx, x, n, block_size, codes, out, cap, out_len, stream)

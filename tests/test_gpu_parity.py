@@ -49,8 +49,8 @@ def _gpu_compress(hz, ctx, x_dev, B, codes=None, cap=None, index=True):
 
 
 def _gpu_decompress(hz, ctx, s_dev, cap=None):
-    if cap is None:
-        cap = oracle.parse_header(s_dev[:280].cpu().numpy())["n"]
+    if cap is None:  # n, from the header bytes themselves
+        cap = int(np.frombuffer(s_dev[8:16].cpu().numpy().tobytes(), dtype="<u8")[0])
     out = torch.empty(max(cap, 1), dtype=torch.uint8, device=DEV)
     out_len = torch.zeros(1, dtype=torch.int64, device=DEV)
     hz.hz_decompress(ctx, s_dev, s_dev.numel(), out, cap, out_len)
@@ -261,29 +261,27 @@ def test_gaussian_field_residuals_small(hz, ctx):
 
 
 @pytest.mark.slow
-def test_mixed_1gib_full_size(hz, ctx):
-    """The 1 GiB workload at full size: every header/index byte and a sample of
-    records against the oracle, plus exact decode of the whole buffer."""
+@pytest.mark.parametrize("sub", [0, 2048])
+def test_mixed_1gib_full_size(hz, ctx, sub):
+    """The 1 GiB workload at full size, in the paper's layout and with sub-block
+    offsets: the whole stream against the oracle's (its OpenMP driver, whose
+    streams equal the sequential oracle's), and exact decode of the whole buffer,
+    by the GPU and by the oracle."""
     x = datagen.mixed_buffer(n=1 << 30, segment=64 * MiB, seed=2, device=DEV)
     B = 65_536
-    st, s, _ = _gpu_compress(hz, ctx, x, B)
-    assert st == 0
+    ctx.set_option(hz.HZ_OPT_SUB_BLOCK, sub)
+    try:
+        s = hz.compress(x, B, ctx=ctx)
+    finally:
+        ctx.set_option(hz.HZ_OPT_SUB_BLOCK, 0)
     x_np = x.cpu().numpy()
-    lengths = oracle.code_lengths(np.bincount(x_np, minlength=256).astype(np.uint64))
+    want = oracle.compress_omp(x_np, B, sub=sub)
     s_np = s.cpu().numpy()
-    hdr = oracle.parse_header(s_np)
-    assert np.array_equal(hdr["lengths"], lengths) and hdr["n"] == x_np.size
-    assert s_np.size == oracle.stream_size(x_np, B, lengths)
-    nb = hdr["nb"]
-    index = s_np[280:280 + 4 * nb].view(np.uint32)
-    blocks_at = 280 + 4 * nb
-    rng = np.random.default_rng(0)
-    for k in sorted(set(rng.integers(0, nb, 48).tolist()) | {0, nb - 1}):
-        words = oracle.encode_block(x_np[k * B:(k + 1) * B], lengths)
-        at = blocks_at + 4 * int(index[k])
-        assert np.array_equal(s_np[at:at + 4 * words.size].view(np.uint32), words), k
+    assert s_np.size == want.size and np.array_equal(s_np, want)
     st, y = _gpu_decompress(hz, ctx, s)
     assert st == 0 and torch.equal(y, x)
+    del y
+    assert np.array_equal(oracle.decompress_omp(s_np), x_np)
 
 
 @pytest.mark.slow

@@ -3,6 +3,9 @@ arrive while others are on the GPU are merged into shared device batches, and
 every result must be the same as the same request run alone -- for results in
 caller buffers, in the replay's device ring, with a ring small enough that
 requests wait for room, and in plain (one launch sequence per request) mode."""
+import concurrent.futures
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -105,13 +108,20 @@ def test_replay_results_equal_alone(hz, workload, burst):
     launches = np.unique(rec["launch"]).size
     if burst:
         assert launches < len(reqs) // 4  # queued requests went out together
-    # a sample of compress results against the oracle, with the tuned block size
+    # every compress result against the oracle, with the tuned block size
     lib = hz.load_library()
-    for i in [k for k, (kind, _) in enumerate(reqs) if kind == "c"][:6]:
-        x = reqs[i][1]
-        B = lib.hz_tuned_block_size(ctx.handle, x.numel())
-        want = oracle.compress(x.cpu().numpy(), B)
-        assert np.array_equal(dsts[i][: int(rec[i]["out_len"])].cpu().numpy(), want)
+    comp = [k for k, (kind, _) in enumerate(reqs) if kind == "c"]
+    assert len(comp) > 100
+
+    def check(i):
+        x = reqs[i][1].cpu().numpy()
+        B = lib.hz_tuned_block_size(ctx.handle, x.size)
+        got = dsts[i][: int(rec[i]["out_len"])].cpu().numpy()
+        return bool(np.array_equal(got, oracle.compress_omp(x, B, threads=1)))
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 8) as ex:
+        same = list(ex.map(check, comp))
+    assert all(same)
     ctx.close()
 
 
