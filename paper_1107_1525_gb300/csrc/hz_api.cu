@@ -35,6 +35,7 @@ struct hz_ctx {
   DecTables* d_dec = nullptr;
   TileStatus* d_tiles = nullptr;
   uint32_t tiles_cap = 0;
+  TileMeta* d_meta = nullptr;  // per-tile metadata for the warp-parallel packer (tiles_cap)
   uint32_t* d_chase = nullptr;
   uint32_t chase_cap = 0;
   uint32_t* h_err = nullptr;  // pinned readback of the status words
@@ -225,6 +226,7 @@ void hz_destroy(hz_ctx* c) {
   cudaFree(c->d_state);
   cudaFree(c->d_dec);
   cudaFree(c->d_tiles);
+  cudaFree(c->d_meta);
   cudaFree(c->d_chase);
   cudaFree(c->d_hin);
   cudaFree(c->d_hout);
@@ -450,10 +452,15 @@ static hz_status encode_setup(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32
     uint64_t cap = c->tiles_cap ? c->tiles_cap : 1024;
     while (cap < ntiles) cap *= 2;
     cudaFree(c->d_tiles);
+    cudaFree(c->d_meta);
     c->d_tiles = nullptr;
+    c->d_meta = nullptr;
     c->tiles_cap = 0;
-    if (cudaMalloc(&c->d_tiles, cap * sizeof(TileStatus)) != cudaSuccess) {
+    if (cudaMalloc(&c->d_tiles, cap * sizeof(TileStatus)) != cudaSuccess ||
+        cudaMalloc(&c->d_meta, cap * sizeof(TileMeta)) != cudaSuccess) {
       cudaGetLastError();
+      cudaFree(c->d_tiles);
+      c->d_tiles = nullptr;
       return HZ_ERR_NOMEM;
     }
     c->tiles_cap = (uint32_t)cap;
@@ -470,6 +477,7 @@ static hz_status encode_setup(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32
   a->sub_M = sub ? B / c->opt_sub : 1;
   a->fdS = make_fastdiv(sub ? c->opt_sub : 1);
   a->spin_limit = c->opt_spin_limit;
+  a->meta = c->d_meta;
   a->out = d_out;
   a->out_cap = out_cap;
   a->out_len = d_out_len;

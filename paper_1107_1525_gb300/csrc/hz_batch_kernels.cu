@@ -79,6 +79,7 @@ __device__ __forceinline__ EncodeArgs comp_args(const BatchComp& c) {
   a.sub_M = 1;
   a.fdS = FastDiv{1, 1, 0, 0};
   a.spin_limit = kSpinLimit;  // (the batched scan runs in one CTA: no waits)
+  a.meta = nullptr;
   return a;
 }
 

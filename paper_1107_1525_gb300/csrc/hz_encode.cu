@@ -30,13 +30,24 @@ namespace hz {
 
 __global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs a) {
   __shared__ uint8_t s_len[256];  // 64 words: random lookups conflict at most 2-way
+  __shared__ uint32_t s_code[256];  // right-aligned codes (warp-parallel path)
+  __shared__ uint8_t s_sym[kEncThreads];  // 32 bytes per warp (warp-parallel path)
   __shared__ uint32_t s_wsum[kEncThreads / 32];
   __shared__ Summary s_warp[kEncThreads / 32];
   const CodeTable* ct = &a.st->codes;
   if (ct->maxlen > (uint32_t)kMaxLen) return;  // code construction failed; already reported
-  for (int s = threadIdx.x; s < 256; s += kEncThreads) s_len[s] = ct->len[s];
+  const bool warps = warp_path(a.meta, a.B, ct->maxlen);
+  for (int s = threadIdx.x; s < 256; s += kEncThreads) {
+    s_len[s] = ct->len[s];
+    s_code[s] = (uint32_t)ct->code[s];
+  }
   __syncthreads();
   bool bad = false;
+  if (warps) {  // uniform
+    count_warps(a, s_len, s_code, s_sym, bad);
+    if (bad) set_error(a.st, HZ_ERR_ARG, 0x200);
+    return;
+  }
   // the next tile's symbols are loaded while the current one is summarised
   uint32_t x[kEncSymPerThread / 4], xn[kEncSymPerThread / 4];
   uint32_t tile = blockIdx.x;
@@ -71,11 +82,14 @@ __global__ void __launch_bounds__(kScanThreads) encode_scan_kernel(EncodeArgs a)
   const uint32_t cta = s_cta;
   const uint32_t nt = a.ntiles;
   const uint32_t t0 = cta * kScanTilesPerCta + tid * kScanPerThread;
+  const bool warps = warp_path(a.meta, a.B, st->codes.maxlen);  // tiles summarised by their metadata
   Summary mine[kScanPerThread];
   Summary agg{0, 0, 0, 0};
 #pragma unroll
   for (int k = 0; k < kScanPerThread; ++k) {
-    mine[k] = t0 + k < nt ? load_summary(a.tiles[t0 + k]) : Summary{0, 0, 0, 0};
+    mine[k] = t0 + k >= nt ? Summary{0, 0, 0, 0}
+              : warps     ? meta_summary(a, t0 + k)
+                          : load_summary(a.tiles[t0 + k]);
     agg = combine(agg, mine[k]);
   }
   Summary inc = agg;
@@ -190,6 +204,12 @@ __global__ void __launch_bounds__(kEncThreads, 4) encode_pack_kernel(EncodeArgs 
   const uint32_t maxlen = a.st->codes.maxlen;
   pack_load_tables(sh, a);
   __syncthreads();
+  // every tile inside one record and codes of at most 16 bits: warps pack on
+  // their own, from the tile metadata of the length-summing pass
+  if (warp_path(a.meta, a.B, maxlen)) {
+    pack_warps_fast(sh);
+    return;
+  }
   for (uint32_t i = blockIdx.x; i < a.tile_end - a.tile_begin; i += gridDim.x) {
     // last tiles first: their input is still in L2 from the length-summing pass
     pack_one_tile(sh, a.tile_end - 1 - i, maxlen);

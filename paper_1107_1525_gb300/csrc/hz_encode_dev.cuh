@@ -155,6 +155,94 @@ static __device__ __forceinline__ void load_tile_symbols(const EncodeArgs& a, ui
 }
 
 // summary_tile with the thread's symbols already loaded.
+// The length-summing pass of the warp-parallel path: every warp of a tile on
+// its own, no CTA barrier.  Records the tile's TileMeta: each lane's bits (the
+// sum of its 32 code lengths), the warp's bits, and the warp's last 32 code
+// bits -- found in parallel: each lane takes one of the last lane's 32
+// symbols, a suffix sum of their lengths places its code, and the codes that
+// end within the last 32 bits are ORed together.  s_len / s_code: lengths and
+// right-aligned codes (shared); s_sym: 32 bytes of per-warp scratch.
+static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const uint8_t* s_len,
+                                                   const uint32_t* s_code, uint8_t* s_sym,
+                                                   bool& bad) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr uint32_t kWarps = kEncThreads / 32;
+  const uint32_t n = (uint32_t)a.n;
+  const uint32_t items = a.ntiles * kWarps;
+  uint8_t* my_sym = s_sym + 32 * warp;
+  for (uint32_t it = blockIdx.x * kWarps + warp; it < items; it += gridDim.x * kWarps) {
+    const uint32_t tile = it / kWarps, w = it % kWarps;
+    const uint32_t lo = tile * (uint32_t)kEncTile;
+    const uint32_t hi = n - lo > (uint32_t)kEncTile ? lo + (uint32_t)kEncTile : n;
+    const uint32_t wlo = lo + w * 32 * kEncSymPerThread;
+    if (wlo >= hi) continue;  // uniform
+    const uint32_t g0 = wlo + lane * kEncSymPerThread;
+    const uint32_t cnt = g0 >= hi ? 0u : min(hi - g0, (uint32_t)kEncSymPerThread);
+    uint32_t x[kEncSymPerThread / 4];
+    load_symbols(a.in + g0, (int)cnt, x);
+    uint32_t bits = 0, minl = 64;
+    if (cnt == kEncSymPerThread) {
+#pragma unroll
+      for (int i = 0; i < kEncSymPerThread; ++i) {
+        const uint32_t l = s_len[sym_of(x, i)];
+        minl = min(minl, l);
+        bits += l;
+      }
+    } else {
+      for (uint32_t i = 0; i < cnt; ++i) {
+        const uint32_t l = s_len[sym_of(x, i)];
+        minl = min(minl, l);
+        bits += l;
+      }
+    }
+    bad |= cnt != 0 && minl == 0;
+    TileMeta& m = a.meta[tile];
+    m.lane_bits[w * 32 + lane] = (uint16_t)bits;
+    uint32_t tot = bits;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, d);
+    // the warp's last 32 bits, when its last lane is full (a later warp needs them)
+    const bool full = __shfl_sync(0xFFFFFFFFu, cnt, 31) == kEncSymPerThread;
+    if (full) {
+      if (lane == 31) {
+#pragma unroll
+        for (int k = 0; k < kEncSymPerThread / 4; ++k)
+          reinterpret_cast<uint32_t*>(my_sym)[k] = x[k];
+      }
+      __syncwarp();
+      const uint32_t sym = my_sym[lane];
+      __syncwarp();
+      const uint32_t l = s_len[sym];
+      uint32_t suf = l;  // lengths of symbols lane .. 31
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_down_sync(0xFFFFFFFFu, suf, d);
+        if (lane + d < 32) suf += o;
+      }
+      const uint32_t after = suf - l;  // bits after my code
+      uint32_t t = after < 32 ? s_code[sym] << after : 0u;
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) t |= __shfl_xor_sync(0xFFFFFFFFu, t, d);
+      if (lane == 0) m.warp_tail[w] = t;
+    }
+    if (lane == 0) m.warp_bits[w] = tot;
+  }
+}
+
+// A tile's summary from its TileMeta (warp-parallel path: the tile lies
+// inside one record).
+static __device__ __forceinline__ Summary meta_summary(const EncodeArgs& a, uint32_t tile) {
+  const TileMeta& m = a.meta[tile];
+  const uint32_t lo = tile * (uint32_t)kEncTile, n = (uint32_t)a.n;
+  const uint32_t syms = n - lo > (uint32_t)kEncTile ? (uint32_t)kEncTile : n - lo;
+  const uint32_t warps = (syms + 32 * kEncSymPerThread - 1) / (32 * kEncSymPerThread);
+  uint32_t total = 0;  // (warps past the input's end hold no symbol and write nothing)
+#pragma unroll
+  for (uint32_t w = 0; w < kEncThreads / 32; ++w) total += w < warps ? m.warp_bits[w] : 0u;
+  const bool starts = fast_mod(tile * (uint32_t)kEncTile, a.fdB) == 0;
+  return starts ? Summary{1, 0, 0, total} : Summary{0, total, 0, 0};
+}
+
 static __device__ __forceinline__ void summary_tile_x(const EncodeArgs& a, uint32_t tile,
                                                       const uint32_t (&x)[kEncSymPerThread / 4],
                                                       const uint8_t* s_len, uint32_t* s_wsum,
@@ -311,6 +399,7 @@ static __device__ __forceinline__ void put_sub_tail(const EncodeArgs& a, uint32_
 struct PackShared {
   EncodeArgs a;         // the launch arguments, read by the per-tile functions
   uint32_t entry[256];  // code << 6 | len, valid for codes of up to 26 bits
+  uint32_t lent[256];   // code << (32 - len) | len, valid for codes of up to 16 bits
   uint32_t len[256];
   uint32_t code_lo[256];
   uint32_t code_hi[256];
@@ -780,6 +869,150 @@ __device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, co
   }
 }
 
+// ------------------------------------------------- warp-parallel packing
+// Tiles that lie inside one record (B a multiple of the tile), codes of at
+// most 16 bits, with the TileMeta the length-summing pass wrote: every warp of
+// a tile packs its 1024 symbols on its own, with no CTA barrier.
+//   - its lanes' bit counts (from the metadata) are scanned with shuffles,
+//     the warp's own offset within the tile and the tile's start state come
+//     from the metadata and the tile scan;
+//   - a lane packs its 32 symbols two codes at a time (a pair is at most 32
+//     bits) into a 64-bit accumulator and writes each word it completes into
+//     the warp's staging area in shared memory;
+//   - the word a lane shares with the lane before it (its first word, when it
+//     starts mid-word) gets that lane's partial last word through one shuffle;
+//     a warp's first word gets the previous warp's last bits from the
+//     metadata's warp tail (the previous warp of the tile, or the last warp of
+//     the tile before);
+//   - a lane's partial last word belongs to the next lane (or warp), except
+//     at the end of the record, where it is written zero-padded;
+//   - the warp copies its words out with 16-byte stores.
+// No word is written twice and the output needs no clearing.
+constexpr uint32_t kWarpStageWords = 520;  // 1024 codes of <= 16 bits, plus alignment
+static_assert(kWarpStageWords * (kEncThreads / 32) <= (uint32_t)kEncStageWords + 4, "staging");
+
+static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
+  const EncodeArgs& a = sh.a;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr uint32_t kWarps = kEncThreads / 32;
+  const uint32_t n = (uint32_t)a.n, B = a.fdB.d;
+  uint32_t* rec_words =
+      reinterpret_cast<uint32_t*>(a.out + records_at(a.nb, a.B, a.flags, a.sub_S));
+  uint32_t* stw = sh.stage + warp * kWarpStageWords;
+  const uint32_t items = (a.tile_end - a.tile_begin) * kWarps;
+  for (uint32_t it = blockIdx.x * kWarps + warp; it < items; it += gridDim.x * kWarps) {
+    // last tiles first: their input is still in L2 from the length-summing pass
+    const uint32_t tile = a.tile_end - 1 - it / kWarps;
+    const uint32_t w = it % kWarps;
+    const uint32_t lo = tile * (uint32_t)kEncTile;
+    const uint32_t hi = n - lo > (uint32_t)kEncTile ? lo + (uint32_t)kEncTile : n;
+    const uint32_t wlo = lo + w * 32 * kEncSymPerThread;
+    if (wlo >= hi) continue;  // uniform: no symbol for this warp
+    const uint32_t g0 = wlo + lane * kEncSymPerThread;
+    const uint32_t cnt = g0 >= hi ? 0u : min(hi - g0, (uint32_t)kEncSymPerThread);
+    uint32_t x[kEncSymPerThread / 4];
+    load_symbols(a.in + g0, (int)cnt, x);
+    const TileMeta& m = a.meta[tile];
+    const bool starts = fast_mod(lo, a.fdB) == 0;
+    const bool ends = fast_mod(hi, a.fdB) == 0 || hi == n;  // the tile ends its record
+    const uint64_t pre_O = a.tiles[tile].pre_O;
+    const uint32_t pre_b = a.tiles[tile].pre_b;
+    const uint64_t O1 = starts ? pre_O + 1 + ceil32(pre_b) : pre_O;  // the record's delimiter
+    const uint32_t b0 = starts ? 0u : pre_b;
+    // my bit position: the tile's start in its record, the warp's prefix, my lanes' prefix
+    const uint32_t c = cnt ? m.lane_bits[w * 32 + lane] : 0u;
+    uint32_t inc = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+      if (lane >= (uint32_t)d) inc += o;
+    }
+    uint32_t wp = 0;  // bits of the tile's earlier warps
+    for (uint32_t v = 0; v < w; ++v) wp += m.warp_bits[v];
+    const uint32_t ws = b0 + wp;  // the warp's first payload bit
+    const uint32_t we = ws + __shfl_sync(0xFFFFFFFFu, inc, 31);
+    const uint32_t p = ws + inc - c;
+    const uint32_t r = ws & 31u;
+    // the last lane with symbols, and whether the record ends with it
+    const uint32_t last_lane = 31u - (__clz(__ballot_sync(0xFFFFFFFFu, cnt > 0)) );
+    const bool rec_end = ends && hi - wlo <= 32u * kEncSymPerThread;  // the warp holds the tile's end
+    // staging: word index i of the payload goes to stw[i - wb + off], so that
+    // 16-byte chunks of stw are 16-byte aligned in the output
+    const uint32_t wb = ws >> 5;
+    uint32_t* pay = rec_words + O1 + 1;
+    const uint32_t off = (uint32_t)(((uintptr_t)(pay + wb)) >> 2) & 3u;
+    // ---- pack: every completed word goes to the staging area (a shared first
+    // word too: the previous lane's bits are ORed into it below)
+    uint32_t acc_hi = 0, acc_lo = 0, nacc = p & 31u;
+    const uint32_t w_first = (p >> 5) - wb + off;
+    uint32_t wi = w_first;
+    const bool shared_head = (p & 31u) != 0 && c != 0;
+    auto push = [&](uint32_t ea, uint32_t eb) {
+      const uint32_t la = ea & 31u;
+      const uint32_t cw = (ea & ~31u) | __funnelshift_rc(eb & ~31u, 0u, la);  // (eb >> la)
+      acc_hi |= cw >> nacc;
+      acc_lo |= __funnelshift_r(0u, cw, nacc);  // cw << (32 - nacc), 0 for nacc = 0
+      nacc += la + (eb & 31u);
+      if (nacc >= 32u) {
+        stw[wi++] = acc_hi;
+        acc_hi = acc_lo;
+        acc_lo = 0;
+        nacc -= 32u;
+      }
+    };
+    if (cnt == kEncSymPerThread) {
+#pragma unroll
+      for (int j = 0; j < kEncSymPerThread / 2; ++j)
+        push(sh.lent[sym_of(x, 2 * j)], sh.lent[sym_of(x, 2 * j + 1)]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kEncSymPerThread / 2; ++j)
+        push((uint32_t)(2 * j) < cnt ? sh.lent[sym_of(x, 2 * j)] : 0u,
+             (uint32_t)(2 * j + 1) < cnt ? sh.lent[sym_of(x, 2 * j + 1)] : 0u);
+    }
+    const bool first = wi == w_first;  // no word completed
+    // ---- the words shared with the lane before (or the warp before)
+    const uint32_t tail = nacc ? acc_hi : 0u;  // my partial last word
+    uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, tail, 1);
+    if (lane == 0) {
+      prev = 0;
+      if (r) {
+        const uint32_t t = w ? m.warp_tail[w - 1] : a.meta[tile - 1].warp_tail[kWarps - 1];
+        prev = (t & ((1u << r) - 1u)) << (32u - r);
+      }
+    }
+    if (shared_head && !first) stw[w_first] |= prev;
+    // a lane that completed no word keeps its bits, and the lane before's, in
+    // `tail`: only the record's last lane can (a full lane holds >= 32 bits)
+    const bool own_tail = lane == last_lane && rec_end;
+    if (own_tail && nacc) stw[wi] = first && shared_head ? (tail | prev) : tail;
+    // ---- delimiter, index, sub-block offsets
+    if (own_tail) {
+      pay[-1] = p + c;  // rec_words[O1]: the record's bit count
+      if ((a.flags & kFlagSub) && hi == n) put_sub_tail(a, p + c);
+    }
+    if (starts && w == 0 && lane == 0 && (a.flags & kFlagIndex))
+      reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[fast_div(lo, a.fdB)] = (uint32_t)O1;
+    if ((a.flags & kFlagSub) && cnt) put_sub_entry(a, g0, p);
+    __syncwarp();
+    // ---- copy out: payload words [wb, wend); the partial last word only at the record's end
+    const uint32_t wend = (we >> 5) + ((rec_end && (we & 31u)) ? 1u : 0u);
+    const uint32_t nw = wend - wb;
+    uint32_t* gbase = pay + wb - off;  // 16-byte aligned
+    for (uint32_t k = lane; 4 * k < nw + off; k += 32) {
+      const uint32_t i0 = 4 * k;
+      if (i0 >= off && i0 + 4 <= nw + off) {
+        *reinterpret_cast<uint4*>(gbase + i0) = *reinterpret_cast<const uint4*>(stw + i0);
+      } else {
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q)
+          if (i0 + q >= off && i0 + q < nw + off) gbase[i0 + q] = stw[i0 + q];
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Load the code table of the buffer `a` describes into the packing tables.
 static __device__ __forceinline__ void pack_load_tables(PackShared& sh, const EncodeArgs& a) {
   const CodeTable* ct = &a.st->codes;
@@ -790,6 +1023,7 @@ static __device__ __forceinline__ void pack_load_tables(PackShared& sh, const En
     sh.code_lo[s] = (uint32_t)c;
     sh.code_hi[s] = (uint32_t)(c >> 32);
     sh.entry[s] = (uint32_t)(c << 6) | l;
+    sh.lent[s] = (l && l <= 16) ? ((uint32_t)c << (32 - l)) | l : 0u;
   }
   if (threadIdx.x == 0) sh.a = a;
 }

@@ -55,6 +55,23 @@ struct TileStatus {
   uint32_t pad1;
 };
 
+// What the length-summing pass records about a tile when every tile lies
+// inside one record and no code is longer than 16 bits (the warp-parallel
+// path): each thread's payload bits (its 32 symbols), each warp's bits, and
+// each warp's last 32 code bits (the bits the next warp's first word
+// continues).  The tile scan sums the warps' bits.
+struct TileMeta {
+  uint16_t lane_bits[kEncThreads];
+  uint32_t warp_bits[kEncThreads / 32];
+  uint32_t warp_tail[kEncThreads / 32];
+};
+
+// The warp-parallel path's condition, the same in every encoder kernel.
+__host__ __device__ __forceinline__ bool warp_path(const TileMeta* meta, uint32_t B,
+                                                   uint32_t maxlen) {
+  return meta != nullptr && B % (uint32_t)kEncTile == 0 && maxlen <= 16;
+}
+
 // The encoder's tile scan runs in CTAs of kScanTilesPerCta tiles; n < 2^32
 // bounds their number.
 constexpr int kScanTilesPerCta = 4096;
@@ -205,6 +222,10 @@ struct EncodeArgs {
   uint32_t sub_S, sub_M;
   FastDiv fdS;              // division by S (S = 1 without bit 1)
   uint32_t spin_limit;      // polls of the scan's look-back before it gives up
+  // per-tile metadata for the warp-parallel packing path (null: not used);
+  // written by the length-summing pass for tiles inside one record when no
+  // code is longer than 16 bits
+  TileMeta* meta;
 };
 
 struct DecodeArgs {

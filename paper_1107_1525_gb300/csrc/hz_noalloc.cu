@@ -104,6 +104,7 @@ extern "C" hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32
     a.sub_M = 1;
     a.fdS = make_fastdiv(1);
     a.spin_limit = kSpinLimit;
+    a.meta = nullptr;  // (no room for it in the fixed scratch)
     if (launch_encode_summary(a, num_sms, s) != cudaSuccess ||
         launch_encode_scan(a, s) != cudaSuccess || launch_encode_pack(a, num_sms, s) != cudaSuccess)
       return HZ_ERR_CUDA;
