@@ -295,6 +295,7 @@ def run_batched(args, hz, dev):
     ctx = hz.Context(dev.index or 0)
     lib = hz.load_library()
     t0 = time.perf_counter()
+    ctx.set_option(hz.HZ_OPT_TUNE_BATCHED, 1)  # tune for batches, the way this workload runs
     hz.hz_autotune(ctx, arena, min(arena.numel(), 256 * MiB))
     tune_s = time.perf_counter() - t0
     tuned = {"block_size_by_class": {c: int(lib.hz_tuned_block_size(ctx.handle, n)) for c, n in
@@ -302,7 +303,8 @@ def run_batched(args, hz, dev):
                                       ("<=16MiB", 16 * MiB), (">16MiB", 64 * MiB))},
              "lut_bits": ctx.get_option(hz.HZ_OPT_DECODE_LUT_BITS),
              "dec_threads": ctx.get_option(hz.HZ_OPT_DECODE_THREADS),
-             "sample": "the first 256 MiB of the batch's buffers", "seconds": tune_s}
+             "sample": "the first 256 MiB of the batch's buffers", "objective": "batched",
+             "seconds": tune_s}
     Bs = np.array([lib.hz_tuned_block_size(ctx.handle, int(n)) for n in lens])
     caps = np.array([hz.hz_compress_bound(int(n), int(b)) for n, b in zip(lens, Bs)])
     coffs = np.zeros(len(lens) + 1, dtype=np.int64)

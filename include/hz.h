@@ -227,6 +227,10 @@ hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32_t block_si
                                  for a predecessor before it records HZ_ERR_TIMEOUT and
                                  returns (1 .. 2^24, default 2^20; each poll sleeps
                                  about 64 ns) */
+#define HZ_OPT_TUNE_BATCHED 11  /* 1: hz_autotune times its block-size candidates on
+                                   batches of slices through hz_submit (the choice for
+                                   batched and served requests) instead of one call
+                                   per slice (default 0) */
 #define HZ_OPT_INJECT_SCAN_STALL 10  /* host-side fault injection for tests: 1 = the
                                  next hz_compress hands its scan CTAs tickets from 1
                                  instead of 0, so the first one waits for a
@@ -245,8 +249,11 @@ int64_t hz_get_option(hz_ctx* ctx, int key);
  * block_size 0, then the decode table width W and the threads per decode
  * CTA, by timing compress + decompress round trips of slices of
  * d_sample[0..n) (device memory, the caller's representative data) for B in
- * {4, 8, 16, 32, 64} KiB, and decompressions of the largest slice for W in
- * {10, 11, 12} and 128 or 256 threads.  Candidates whose format overhead
+ * {4, 8, 16, 32, 64} KiB -- one call per slice, or with HZ_OPT_TUNE_BATCHED
+ * batches of up to 64 slices through hz_submit -- and decompressions of the
+ * largest slice for W in {10, 11, 12} and 128 or 256 threads.  A candidate
+ * replaces the default (the built-in block size, W = 12, 256 threads) only
+ * when it is more than 3 % faster.  Candidates whose format overhead
  * (Sec. 2.1: 32-63 bits per block) exceeds 1 % of the stream are skipped.  The choice is kept in the
  * context and, when the environment variable HZ_TUNE_CACHE names a file,
  * written there as JSON; hz_create loads that file when it exists.

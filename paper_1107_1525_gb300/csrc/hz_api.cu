@@ -63,6 +63,7 @@ struct hz_ctx {
   uint32_t opt_sub = 0;  // symbols per sub-block for the sub-block offsets, 0 = none
   uint32_t opt_spin_limit = kSpinLimit;
   bool inject_scan_stall = false;  // one shot: the next scan's tickets start at 1
+  int opt_tune_batched = 0;
   int opt_profile = 0;
   int opt_lut_bits = 12;
   int opt_dec_threads = 256;
@@ -275,6 +276,10 @@ hz_status hz_set_option(hz_ctx* c, int key, int64_t v) {
       if (v != 0 && v != 1) return HZ_ERR_ARG;
       c->inject_scan_stall = v != 0;
       return HZ_OK;
+    case HZ_OPT_TUNE_BATCHED:
+      if (v != 0 && v != 1) return HZ_ERR_ARG;
+      c->opt_tune_batched = (int)v;
+      return HZ_OK;
     case HZ_OPT_SUB_BLOCK:
       if (v != 0 && (v < 32 || v % 32 != 0 || v > (int64_t)kMaxBlock)) return HZ_ERR_ARG;
       c->opt_sub = (uint32_t)v;
@@ -309,6 +314,7 @@ int64_t hz_get_option(hz_ctx* c, int key) {
     case HZ_OPT_INDEX: return c->opt_index;
     case HZ_OPT_PROFILE: return c->opt_profile;
     case HZ_OPT_SUB_BLOCK: return c->opt_sub;
+    case HZ_OPT_TUNE_BATCHED: return c->opt_tune_batched;
     case HZ_OPT_SPIN_LIMIT: return c->opt_spin_limit;
     case HZ_OPT_INJECT_SCAN_STALL: return c->inject_scan_stall ? 1 : 0;
     case HZ_OPT_DECODE_LUT_BITS: return c->opt_lut_bits;

@@ -181,15 +181,9 @@ static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const ui
     uint32_t x[kEncSymPerThread / 4];
     load_symbols(a.in + g0, (int)cnt, x);
     uint32_t bits = 0, minl = 64;
-    if (cnt == kEncSymPerThread) {
 #pragma unroll
-      for (int i = 0; i < kEncSymPerThread; ++i) {
-        const uint32_t l = s_len[sym_of(x, i)];
-        minl = min(minl, l);
-        bits += l;
-      }
-    } else {
-      for (uint32_t i = 0; i < cnt; ++i) {
+    for (int i = 0; i < kEncSymPerThread; ++i) {  // (static indices: x stays in registers)
+      if (cnt == kEncSymPerThread || (uint32_t)i < cnt) {
         const uint32_t l = s_len[sym_of(x, i)];
         minl = min(minl, l);
         bits += l;
@@ -895,7 +889,7 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
   const EncodeArgs& a = sh.a;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr uint32_t kWarps = kEncThreads / 32;
-  const uint32_t n = (uint32_t)a.n, B = a.fdB.d;
+  const uint32_t n = (uint32_t)a.n;
   uint32_t* rec_words =
       reinterpret_cast<uint32_t*>(a.out + records_at(a.nb, a.B, a.flags, a.sub_S));
   uint32_t* stw = sh.stage + warp * kWarpStageWords;

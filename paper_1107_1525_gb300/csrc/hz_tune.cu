@@ -2,14 +2,18 @@
 // and its JSON cache.
 //
 // Per input-size class it times compress + decompress round trips of a slice
-// of the caller's sample for every candidate block size, keeps the fastest
-// one whose per-block format overhead stays within 1 % (Sec. 2.1: each block
-// costs 32-63 bits), and then times the decoder's table width and its CTA
-// width on the largest class.  The result lives in the context; HZ_TUNE_CACHE names a file that
+// of the caller's sample for every candidate block size (or, with
+// HZ_OPT_TUNE_BATCHED, batches of such slices through hz_submit), keeps the
+// fastest one whose per-block format overhead stays within 1 % (Sec. 2.1:
+// each block costs 32-63 bits) -- a candidate must beat the default by 3 % --
+// and then times the decoder's table width and its CTA width on the largest
+// class the same way.  The result lives in the context; HZ_TUNE_CACHE names a file that
 // stores it across processes.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include <chrono>
 
 #include "hz_internal.cuh"
 
@@ -17,6 +21,11 @@ uint32_t hz_ctx_block_size(hz_ctx* c, uint64_t n);
 void hz_ctx_set_tuned(hz_ctx* c, const uint32_t* B, int lut_bits, int dec_threads);
 void hz_ctx_get_tuned(hz_ctx* c, uint32_t* B, int* lut_bits, int* dec_threads);
 int hz_ctx_device(hz_ctx* c);
+uint32_t hz_batch_tuned_block_size(uint64_t n);
+
+// A candidate replaces the current choice only when it is faster by more than
+// this fraction: timing noise alone must not move a choice.
+constexpr float kTuneMargin = 0.03f;
 
 namespace {
 
@@ -110,22 +119,70 @@ extern "C" hz_status hz_autotune(hz_ctx* c, const uint8_t* d_sample, uint64_t n,
     if (st == HZ_OK) cudaEventElapsedTime(ms, e0, e1);
     return st;
   };
+  // Batched objective: a class's slices go through hz_submit as one batch of
+  // up to kBatchSlices requests (compress, then decompress of the streams).
+  const bool batched = hz_get_option(c, HZ_OPT_TUNE_BATCHED) != 0;
+  constexpr uint32_t kBatchSlices = 64;
+  auto batch_trip = [&](uint64_t m, uint32_t B, int iters, float* ms, uint64_t* len) -> hz_status {
+    const uint32_t k = (uint32_t)(n / m < kBatchSlices ? n / m : kBatchSlices);
+    const uint64_t scap = hz_compress_bound_ctx(c, m, B);
+    if (k == 0 || (uint64_t)k * scap > cap || (uint64_t)k * m > m_max) return HZ_ERR_ARG;
+    hz_request rq[kBatchSlices];
+    uint64_t lens[kBatchSlices];
+    hz_status per[kBatchSlices];
+    auto run = [&](int op) -> hz_status {
+      for (uint32_t i = 0; i < k; ++i) {
+        rq[i].op = op;
+        rq[i].block_size = B;
+        rq[i].d_src = op == HZ_OP_COMPRESS ? d_sample + i * m : d_out + i * scap;
+        rq[i].src_len = op == HZ_OP_COMPRESS ? m : lens[i];
+        rq[i].d_dst = op == HZ_OP_COMPRESS ? d_out + i * scap : d_dec + i * m;
+        rq[i].dst_cap = op == HZ_OP_COMPRESS ? scap : m;
+      }
+      uint64_t t = 0;
+      hz_status st = hz_submit(c, rq, k, &t, s);
+      if (st == HZ_OK) st = hz_poll(c, t, -1, per, op == HZ_OP_COMPRESS ? lens : nullptr);
+      for (uint32_t i = 0; st == HZ_OK && i < k; ++i)
+        if (per[i] != HZ_OK) st = per[i];
+      return st;
+    };
+    hz_status st = run(HZ_OP_COMPRESS);  // warm-up; also the streams' sizes
+    if (st == HZ_OK) st = run(HZ_OP_DECOMPRESS);
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < k; ++i) total += lens[i];
+    *len = total / k;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int it = 0; it < iters && st == HZ_OK; ++it) {
+      st = run(HZ_OP_COMPRESS);
+      if (st == HZ_OK) st = run(HZ_OP_DECOMPRESS);
+    }
+    *ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+  };
   for (int k = 0; k < 4 && result == HZ_OK; ++k) {
     const uint64_t m = n < kClassSize[k] ? n : kClassSize[k];
     const int iters = (int)((256ull << 20) / m) < 1 ? 1 : ((256ull << 20) / m > 64 ? 64 : (int)((256ull << 20) / m));
+    const int biters = iters / 16 > 2 ? iters / 16 : 2;
+    // the default (the built-in size table) is the choice to beat
+    const uint32_t B0 = hz_batch_tuned_block_size(m);
     float best = 1e30f;
-    best_B[k] = hz_ctx_block_size(c, m);
-    for (uint32_t B : kCandB) {
-      float ms = 0;
-      uint64_t len = 0;
-      // warm-up, then the timed round trips
-      if (round_trip(m, B, 1, &ms, &len) != HZ_OK) continue;
-      const uint64_t nb = (m + B - 1) / B;
-      if (nb * 8 > len / 100) continue;  // up to 63 bits + delimiter per block: keep within 1 %
-      if (round_trip(m, B, iters, &ms, &len) != HZ_OK) continue;
-      if (ms < best) {
-        best = ms;
-        best_B[k] = B;
+    best_B[k] = B0;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (uint32_t B : kCandB) {
+        if ((pass == 0) != (B == B0)) continue;  // the default first
+        float ms = 0;
+        uint64_t len = 0;
+        // warm-up, then the timed round trips
+        if (!batched && round_trip(m, B, 1, &ms, &len) != HZ_OK) continue;
+        const uint64_t nb = (m + B - 1) / B;
+        if (batched ? batch_trip(m, B, biters, &ms, &len) != HZ_OK
+                    : (nb * 8 > len / 100 || round_trip(m, B, iters, &ms, &len) != HZ_OK))
+          continue;
+        if (nb * 8 > len / 100) continue;  // up to 63 bits + delimiter per block: keep within 1 %
+        if (ms < best * (pass == 0 ? 1.0f : 1.0f - kTuneMargin)) {
+          best = ms;
+          best_B[k] = B;
+        }
       }
     }
   }
@@ -148,11 +205,16 @@ extern "C" hz_status hz_autotune(hz_ctx* c, const uint8_t* d_sample, uint64_t n,
       return ms;
     };
     if (hz_sync(c, s) == HZ_OK) {
+      // the defaults (W = 12, 256 threads) are the choices to beat, by the margin
       hz_set_option(c, HZ_OPT_DECODE_THREADS, 256);
+      hz_set_option(c, HZ_OPT_DECODE_LUT_BITS, 12);
+      best = time_decode();
+      best_W = 12;
       for (int W : kCandW) {
+        if (W == 12) continue;
         hz_set_option(c, HZ_OPT_DECODE_LUT_BITS, W);
         const float ms = time_decode();
-        if (ms < best) {
+        if (ms < best * (1.0f - kTuneMargin)) {
           best = ms;
           best_W = W;
         }
@@ -162,7 +224,7 @@ extern "C" hz_status hz_autotune(hz_ctx* c, const uint8_t* d_sample, uint64_t n,
       for (int T : kCandThreads) {
         hz_set_option(c, HZ_OPT_DECODE_THREADS, T);
         const float ms = time_decode();
-        if (ms < best) {
+        if (ms < best * (T == 256 ? 1.0f : 1.0f - kTuneMargin)) {
           best = ms;
           best_T = T;
         }
