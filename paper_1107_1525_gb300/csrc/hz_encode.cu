@@ -30,8 +30,11 @@ namespace hz {
 
 __global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs a) {
   __shared__ uint8_t s_len[256];  // 64 words: random lookups conflict at most 2-way
-  __shared__ uint32_t s_code[256];  // right-aligned codes (warp-parallel path)
-  __shared__ uint8_t s_sym[kEncThreads];  // 32 bytes per warp (warp-parallel path)
+  // warp-parallel path: the lengths once per lane in the lane's own bank, the
+  // right-aligned codes, 32 bytes of scratch per warp
+  extern __shared__ uint32_t s_len32[];  // 256 * 32 words (dynamic, that path only)
+  __shared__ uint32_t s_code[256];
+  __shared__ uint8_t s_sym[kEncThreads];
   __shared__ uint32_t s_wsum[kEncThreads / 32];
   __shared__ Summary s_warp[kEncThreads / 32];
   const CodeTable* ct = &a.st->codes;
@@ -41,10 +44,13 @@ __global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs 
     s_len[s] = ct->len[s];
     s_code[s] = (uint32_t)ct->code[s];
   }
+  if (warps) {
+    for (int i = threadIdx.x; i < 256 * 32; i += kEncThreads) s_len32[i] = ct->len[i >> 5];
+  }
   __syncthreads();
   bool bad = false;
   if (warps) {  // uniform
-    count_warps(a, s_len, s_code, s_sym, bad);
+    count_warps(a, s_len32, s_code, s_sym, bad);
     if (bad) set_error(a.st, HZ_ERR_ARG, 0x200);
     return;
   }
@@ -217,11 +223,24 @@ __global__ void __launch_bounds__(kEncThreads, 4) encode_pack_kernel(EncodeArgs 
   }
 }
 
+static PerDeviceSetup<1> g_summary_setup;
+
 cudaError_t launch_encode_summary(const EncodeArgs& a, int num_sms, cudaStream_t s) {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_summary_kernel, kEncThreads, 0);
-  const uint64_t grid = (uint64_t)num_sms * (per_sm > 0 ? per_sm : 1);
-  encode_summary_kernel<<<(unsigned)(grid < a.ntiles ? grid : a.ntiles), kEncThreads, 0, s>>>(a);
+  // dynamic shared memory for the lane-private length copies of the
+  // warp-parallel path (whether the path applies is decided on the device)
+  const int smem = a.meta ? 256 * 32 * 4 : 0;
+  int per_sm = 1;
+  const cudaError_t e = launch_setup_per_device(g_summary_setup, 0, &per_sm, [&](int& out) {
+    cudaError_t r = cudaFuncSetAttribute(encode_summary_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 32 * 4);
+    if (r == cudaSuccess)
+      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, encode_summary_kernel, kEncThreads,
+                                                        256 * 32 * 4);
+    return r;
+  });
+  if (e != cudaSuccess) return e;
+  const uint64_t grid = (uint64_t)num_sms * per_sm;
+  encode_summary_kernel<<<(unsigned)(grid < a.ntiles ? grid : a.ntiles), kEncThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -160,31 +160,55 @@ static __device__ __forceinline__ void load_tile_symbols(const EncodeArgs& a, ui
 // sum of its 32 code lengths), the warp's bits, and the warp's last 32 code
 // bits -- found in parallel: each lane takes one of the last lane's 32
 // symbols, a suffix sum of their lengths places its code, and the codes that
-// end within the last 32 bits are ORed together.  s_len / s_code: lengths and
-// right-aligned codes (shared); s_sym: 32 bytes of per-warp scratch.
-static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const uint8_t* s_len,
+// end within the last 32 bits are ORed together.  s_len32: the lengths kept
+// once per lane, in the lane's own bank (entry s of lane l at word 32 s + l),
+// so that 32 lanes' lookups are one shared-memory wavefront, as the
+// histogram's counters are; s_code: right-aligned codes; s_sym: 32 bytes of
+// per-warp scratch.
+static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const uint32_t* s_len32,
                                                    const uint32_t* s_code, uint8_t* s_sym,
                                                    bool& bad) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // this lane's copy of the lengths: entry s at word 32 s + lane, in the lane's own bank
+  const uint32_t* my_len = s_len32 + lane;
   constexpr uint32_t kWarps = kEncThreads / 32;
   const uint32_t n = (uint32_t)a.n;
   const uint32_t items = a.ntiles * kWarps;
+  const uint32_t stride = gridDim.x * kWarps;
   uint8_t* my_sym = s_sym + 32 * warp;
-  for (uint32_t it = blockIdx.x * kWarps + warp; it < items; it += gridDim.x * kWarps) {
-    const uint32_t tile = it / kWarps, w = it % kWarps;
-    const uint32_t lo = tile * (uint32_t)kEncTile;
+  // item it's symbols for this lane (g0, cnt); false when the warp has none
+  auto geometry = [&](uint32_t it, uint32_t& g0, uint32_t& cnt) -> bool {
+    const uint32_t lo = (it / kWarps) * (uint32_t)kEncTile;
     const uint32_t hi = n - lo > (uint32_t)kEncTile ? lo + (uint32_t)kEncTile : n;
-    const uint32_t wlo = lo + w * 32 * kEncSymPerThread;
-    if (wlo >= hi) continue;  // uniform
-    const uint32_t g0 = wlo + lane * kEncSymPerThread;
-    const uint32_t cnt = g0 >= hi ? 0u : min(hi - g0, (uint32_t)kEncSymPerThread);
-    uint32_t x[kEncSymPerThread / 4];
-    load_symbols(a.in + g0, (int)cnt, x);
+    const uint32_t wlo = lo + (it % kWarps) * 32 * kEncSymPerThread;
+    g0 = wlo + lane * kEncSymPerThread;
+    cnt = g0 >= hi ? 0u : min(hi - g0, (uint32_t)kEncSymPerThread);
+    return wlo < hi;
+  };
+  // the next item's symbols are loaded while the current one is summed
+  uint32_t it = blockIdx.x * kWarps + warp;
+  uint32_t g0 = 0, cnt = 0;
+  bool has = it < items && geometry(it, g0, cnt);
+  uint32_t x[kEncSymPerThread / 4], xn[kEncSymPerThread / 4];
+  if (has) load_symbols(a.in + g0, (int)cnt, x);
+  for (; it < items; it += stride) {
+    uint32_t ng0 = 0, ncnt = 0;
+    const bool nhas = it + stride < items && geometry(it + stride, ng0, ncnt);
+    if (nhas) load_symbols(a.in + ng0, (int)ncnt, xn);
+    if (!has) {  // uniform
+#pragma unroll
+      for (int k = 0; k < kEncSymPerThread / 4; ++k) x[k] = xn[k];
+      has = nhas;
+      g0 = ng0;
+      cnt = ncnt;
+      continue;
+    }
+    const uint32_t tile = it / kWarps, w = it % kWarps;
     uint32_t bits = 0, minl = 64;
 #pragma unroll
     for (int i = 0; i < kEncSymPerThread; ++i) {  // (static indices: x stays in registers)
       if (cnt == kEncSymPerThread || (uint32_t)i < cnt) {
-        const uint32_t l = s_len[sym_of(x, i)];
+        const uint32_t l = my_len[sym_of(x, i) << 5];
         minl = min(minl, l);
         bits += l;
       }
@@ -206,7 +230,7 @@ static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const ui
       __syncwarp();
       const uint32_t sym = my_sym[lane];
       __syncwarp();
-      const uint32_t l = s_len[sym];
+      const uint32_t l = my_len[sym << 5];
       uint32_t suf = l;  // lengths of symbols lane .. 31
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -220,6 +244,11 @@ static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const ui
       if (lane == 0) m.warp_tail[w] = t;
     }
     if (lane == 0) m.warp_bits[w] = tot;
+#pragma unroll
+    for (int k = 0; k < kEncSymPerThread / 4; ++k) x[k] = xn[k];
+    has = nhas;
+    g0 = ng0;
+    cnt = ncnt;
   }
 }
 
