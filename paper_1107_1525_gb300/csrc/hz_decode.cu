@@ -64,6 +64,35 @@ __device__ __noinline__ void decode_generic_blocks(const DecodeArgs& a, const De
     decode_block_generic<NT>(a, g.sh, g.bs, k);
 }
 
+// Streams with sub-block offsets (flags bit 1): a lane per sub-block, in one
+// pass, inside decode_fast_kernel (one launch per decompression whatever the
+// layout).  The common table mode (mode 0 with the replicated 10-bit table)
+// runs inlined, with the registers of the kernel itself; the other modes
+// call their separate functions.
+static __device__ __forceinline__ void decode_sub_blocks(const DecodeArgs& a, const DecTables* T) {
+  const uint32_t warps = blockDim.x / 32;
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint32_t nb = T->nb;
+  const uint32_t k_end = a.k_end < nb ? a.k_end : nb;
+  const uint32_t M = T->sub_M;
+  const uint32_t u_begin = a.k_begin * M, u_end = k_end * M;
+  if (u_begin + 32 * blockIdx.x * warps >= u_end) return;  // uniform: nothing for this CTA
+  FastShared& sh = fast_sh();
+  load_fast_tables(sh, T, threadIdx.x, blockDim.x);
+  if (threadIdx.x == 0) sh.args = a;
+  __syncthreads();
+  const int mode = fast_mode(T, sh.c);
+  const uint32_t first = u_begin + 32 * (blockIdx.x * warps + warp);
+  const uint32_t step = 32 * gridDim.x * warps;
+  if (mode == 0 && sh.fill_k == 3) {
+    for (uint32_t u0 = first; u0 < u_end; u0 += step) decode_units0_body<3, true>(u0, u_end);
+  } else if (mode == 0 && sh.fill_k == 4) {
+    for (uint32_t u0 = first; u0 < u_end; u0 += step) decode_units0_body<4, true>(u0, u_end);
+  } else {
+    for (uint32_t u0 = first; u0 < u_end; u0 += step) decode_units_fast(u0, u_end, mode);
+  }
+}
+
 // Launched with 128 or 256 threads and decode_smem_bytes(threads) of dynamic
 // shared memory.  With at least as many blocks as the launch has warps, warp j
 // of CTA i takes block k_begin + i * warps + j (a CTA's warps read adjacent
@@ -77,7 +106,10 @@ __global__ void __launch_bounds__(kFastThreads, 3) decode_fast_kernel(DecodeArgs
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t nb = T->nb;
   const uint32_t k_end = a.k_end < nb ? a.k_end : nb;
-  if (T->sub_M) return;  // sub-block offsets: decode_sub_kernel decodes this stream
+  if (T->sub_M) {  // uniform: sub-block offsets, a lane per sub-block
+    decode_sub_blocks(a, T);
+    return;
+  }
   if (!fast_block_size(T->B)) {  // uniform: every CTA takes whole blocks
     if (blockDim.x == 128) decode_generic_blocks<128>(a, T);
     else decode_generic_blocks<kFastThreads>(a, T);
@@ -94,39 +126,6 @@ __global__ void __launch_bounds__(kFastThreads, 3) decode_fast_kernel(DecodeArgs
   for (uint32_t k = k0; k < k_end; k += stride) decode_block_fast(a, k, mode);
 }
 
-// Streams with sub-block offsets (flags bit 1): a lane per sub-block, in one
-// pass.  CTAs of kSubThreads threads, three per SM.  The common table mode
-// (mode 0 with the replicated 10-bit table) runs inlined, with the registers
-// of the kernel itself; the others call their separate functions.  Launched
-// after decode_fast_kernel on every decompression; whichever of the two does
-// not suit the stream returns at once.
-constexpr int kSubThreads = 256;
-__global__ void __launch_bounds__(kSubThreads, 3) decode_sub_kernel(DecodeArgs a,
-                                                                 const DecTables* T) {
-  if (!T->ok || !T->sub_M) return;  // uniform
-  const uint32_t warps = kSubThreads / 32;
-  const uint32_t warp = threadIdx.x >> 5;
-  const uint32_t nb = T->nb;
-  const uint32_t k_end = a.k_end < nb ? a.k_end : nb;
-  const uint32_t M = T->sub_M;
-  const uint32_t u_begin = a.k_begin * M, u_end = k_end * M;
-  if (u_begin + 32 * blockIdx.x * warps >= u_end) return;  // uniform: nothing for this CTA
-  FastShared& sh = fast_sh();
-  load_fast_tables(sh, T, threadIdx.x, kSubThreads);
-  if (threadIdx.x == 0) sh.args = a;
-  __syncthreads();
-  const int mode = fast_mode(T, sh.c);
-  const uint32_t first = u_begin + 32 * (blockIdx.x * warps + warp);
-  const uint32_t step = 32 * gridDim.x * warps;
-  if (mode == 0 && sh.fill_k == 3) {
-    for (uint32_t u0 = first; u0 < u_end; u0 += step) decode_units0_body<3, true>(u0, u_end);
-  } else if (mode == 0 && sh.fill_k == 4) {
-    for (uint32_t u0 = first; u0 < u_end; u0 += step) decode_units0_body<4, true>(u0, u_end);
-  } else {
-    for (uint32_t u0 = first; u0 < u_end; u0 += step) decode_units_fast(u0, u_end, mode);
-  }
-}
-
 size_t decode_smem_bytes(int threads) {
   const size_t fast = fast_smem_bytes(threads);
   const size_t gen = threads == 128 ? sizeof(GenAll<128>) : sizeof(GenAll<kFastThreads>);
@@ -135,7 +134,6 @@ size_t decode_smem_bytes(int threads) {
 
 // ================================================================ launchers
 static PerDeviceSetup<2> g_decode_setup;
-static PerDeviceSetup<1> g_sub_setup;
 
 cudaError_t launch_decode_setup(const DecodeArgs& a, DecTables* T, cudaStream_t s) {
   decode_setup_kernel<<<1, 256, 0, s>>>(a, T);
@@ -168,22 +166,6 @@ cudaError_t launch_decode_blocks(const DecodeArgs& a, const DecTables* T, int th
     if (need < grid) grid = need ? need : 1;
   }
   decode_fast_kernel<<<(unsigned)grid, threads, smem, s>>>(a, T);
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
-  // streams with sub-block offsets
-  const size_t sub_smem = fast_smem_bytes(kSubThreads);
-  int sub_per_sm = 1;
-  err = launch_setup_per_device(g_sub_setup, 0, &sub_per_sm, [&](int& out) {
-    cudaError_t r = cudaFuncSetAttribute(decode_sub_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sub_smem);
-    if (r == cudaSuccess)
-      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, decode_sub_kernel, kSubThreads,
-                                                        sub_smem);
-    return r;
-  });
-  if (err != cudaSuccess) return err;
-  decode_sub_kernel<<<(unsigned)((uint64_t)num_sms * sub_per_sm), kSubThreads, sub_smem, s>>>(a, T);
   return cudaGetLastError();
 }
 
