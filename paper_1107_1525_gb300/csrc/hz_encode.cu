@@ -45,7 +45,10 @@ __global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs 
     s_code[s] = (uint32_t)ct->code[s];
   }
   if (warps) {
-    for (int i = threadIdx.x; i < 256 * 32; i += kEncThreads) s_len32[i] = ct->len[i >> 5];
+    for (int i = threadIdx.x; i < 256 * 32; i += kEncThreads) {
+      const uint32_t l = ct->len[i >> 5];
+      s_len32[i] = l ? l : kLenNoCode;
+    }
   }
   __syncthreads();
   bool bad = false;

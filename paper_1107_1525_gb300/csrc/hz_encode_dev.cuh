@@ -165,6 +165,7 @@ static __device__ __forceinline__ void load_tile_symbols(const EncodeArgs& a, ui
 // so that 32 lanes' lookups are one shared-memory wavefront, as the
 // histogram's counters are; s_code: right-aligned codes; s_sym: 32 bytes of
 // per-warp scratch.
+constexpr uint32_t kLenNoCode = 1u << 16;  // > 32 codes of at most 16 bits
 static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const uint32_t* s_len32,
                                                    const uint32_t* s_code, uint8_t* s_sym,
                                                    bool& bad) {
@@ -204,21 +205,21 @@ static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const ui
       continue;
     }
     const uint32_t tile = it / kWarps, w = it % kWarps;
-    uint32_t bits = 0, minl = 64;
+    // (static indices: x stays in registers; a byte without a code counts
+    // kLenNoCode, which no sum of real lengths reaches)
+    uint32_t bits = 0;
+    if (cnt == kEncSymPerThread) {
 #pragma unroll
-    for (int i = 0; i < kEncSymPerThread; ++i) {  // (static indices: x stays in registers)
-      if (cnt == kEncSymPerThread || (uint32_t)i < cnt) {
-        const uint32_t l = my_len[sym_of(x, i) << 5];
-        minl = min(minl, l);
-        bits += l;
-      }
+      for (int i = 0; i < kEncSymPerThread; ++i) bits += my_len[sym_of(x, i) << 5];
+    } else {
+#pragma unroll
+      for (int i = 0; i < kEncSymPerThread; ++i)
+        if ((uint32_t)i < cnt) bits += my_len[sym_of(x, i) << 5];
     }
-    bad |= cnt != 0 && minl == 0;
+    bad |= bits >= kLenNoCode;
     TileMeta& m = a.meta[tile];
     m.lane_bits[w * 32 + lane] = (uint16_t)bits;
-    uint32_t tot = bits;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, d);
+    const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, bits);
     // the warp's last 32 bits, when its last lane is full (a later warp needs them)
     const bool full = __shfl_sync(0xFFFFFFFFu, cnt, 31) == kEncSymPerThread;
     if (full) {
@@ -238,9 +239,7 @@ static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const ui
         if (lane + d < 32) suf += o;
       }
       const uint32_t after = suf - l;  // bits after my code
-      uint32_t t = after < 32 ? s_code[sym] << after : 0u;
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) t |= __shfl_xor_sync(0xFFFFFFFFu, t, d);
+      const uint32_t t = __reduce_or_sync(0xFFFFFFFFu, after < 32 ? s_code[sym] << after : 0u);
       if (lane == 0) m.warp_tail[w] = t;
     }
     if (lane == 0) m.warp_bits[w] = tot;
@@ -950,8 +949,8 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
       const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
       if (lane >= (uint32_t)d) inc += o;
     }
-    uint32_t wp = 0;  // bits of the tile's earlier warps
-    for (uint32_t v = 0; v < w; ++v) wp += m.warp_bits[v];
+    // bits of the tile's earlier warps: lane v < w loads warp v's count
+    const uint32_t wp = __reduce_add_sync(0xFFFFFFFFu, lane < w ? m.warp_bits[lane] : 0u);
     const uint32_t ws = b0 + wp;  // the warp's first payload bit
     const uint32_t we = ws + __shfl_sync(0xFFFFFFFFu, inc, 31);
     const uint32_t p = ws + inc - c;
