@@ -1336,7 +1336,9 @@ __device__ __forceinline__ void decode_units0_body(uint32_t u0, uint32_t u_end) 
     }
   }
   // 32 symbols per 32-byte store (one whole sector per write request), a
-  // refill point every 16
+  // refill point every 16 steps, a fill every K2 steps counted over the 32
+  // (the last fill of a group is at most K2 - 1 steps before the next
+  // group's first)
   while (__any_sync(0xFFFFFFFFu, rem >= 32)) {
     if (rem >= 32) {
       uint32_t q[8];
@@ -1345,15 +1347,15 @@ __device__ __forceinline__ void decode_units0_body(uint32_t u0, uint32_t u_end) 
         w.refill<false>();
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          uint32_t word = 0;
+          uint32_t h[4];
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
-            if ((4 * j + b) % K2 == 0) w.fill0();
-            const uint32_t h = step();
-            // byte b of the word <- the symbol (byte 1 of h)
-            word = __byte_perm(word, h, b == 0 ? 0x3215u : b == 1 ? 0x3250u : b == 2 ? 0x3510u : 0x5210u);
+            if ((16 * half + 4 * j + b) % K2 == 0) w.fill0();
+            h[b] = step();
           }
-          q[4 * half + j] = word;
+          // the four symbols (byte 1 of each h) into one word, two at a time
+          q[4 * half + j] = __byte_perm(__byte_perm(h[0], h[1], 0x0051u),
+                                        __byte_perm(h[2], h[3], 0x0051u), 0x5410u);
         }
       }
       st_global_v8(dst, q);
