@@ -157,8 +157,9 @@ static __device__ __forceinline__ void load_tile_symbols(const EncodeArgs& a, ui
 // summary_tile with the thread's symbols already loaded.
 // The length-summing pass of the warp-parallel path: every warp of a tile on
 // its own, no CTA barrier.  Records the tile's TileMeta: each lane's bits (the
-// sum of its 32 code lengths), the warp's bits, and the warp's last 32 code
-// bits -- found in parallel: each lane takes one of the last lane's 32
+// sum of its 32 code lengths), the warp's bits, and, for the odd runs of a
+// tile (the ones a packing item starts after), the warp's last 32 code bits
+// -- found in parallel: each lane takes one of the last lane's 32
 // symbols, a suffix sum of their lengths places its code, and the codes that
 // end within the last 32 bits are ORed together.  s_len32: the lengths kept
 // once per lane, in the lane's own bank (entry s of lane l at word 32 s + l),
@@ -220,9 +221,11 @@ static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const ui
     TileMeta& m = a.meta[tile];
     m.lane_bits[w * 32 + lane] = (uint16_t)bits;
     const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, bits);
-    // the warp's last 32 bits, when its last lane is full (a later warp needs them)
+    // the warp's last 32 bits, when its last lane is full and the packer
+    // starts a warp item after it (it packs two of these runs per item, so
+    // only the odd runs' tails are read)
     const bool full = __shfl_sync(0xFFFFFFFFu, cnt, 31) == kEncSymPerThread;
-    if (full) {
+    if (full && (w & 1u)) {
       if (lane == 31) {
 #pragma unroll
         for (int k = 0; k < kEncSymPerThread / 4; ++k)
@@ -893,24 +896,31 @@ __device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, co
 
 // ------------------------------------------------- warp-parallel packing
 // Tiles that lie inside one record (B a multiple of the tile), codes of at
-// most 16 bits, with the TileMeta the length-summing pass wrote: every warp of
-// a tile packs its 1024 symbols on its own, with no CTA barrier.
-//   - its lanes' bit counts (from the metadata) are scanned with shuffles,
-//     the warp's own offset within the tile and the tile's start state come
-//     from the metadata and the tile scan;
-//   - a lane packs its 32 symbols two codes at a time (a pair is at most 32
+// most 16 bits, with the TileMeta the length-summing pass wrote: a warp packs
+// 2048 symbols of a tile (two of the summing pass's 1024-symbol runs) on its
+// own, with no CTA barrier.
+//   - lane l takes the 64 symbols of the summing pass's 32-symbol runs 2l and
+//     2l + 1; their bit counts (from the metadata, one 32-bit load) are
+//     scanned with shuffles, the warp's own offset within the tile and the
+//     tile's start state come from the metadata and the tile scan;
+//   - a lane packs its symbols two codes at a time (a pair is at most 32
 //     bits) into a 64-bit accumulator and writes each word it completes into
 //     the warp's staging area in shared memory;
 //   - the word a lane shares with the lane before it (its first word, when it
 //     starts mid-word) gets that lane's partial last word through one shuffle;
-//     a warp's first word gets the previous warp's last bits from the
-//     metadata's warp tail (the previous warp of the tile, or the last warp of
+//     a warp's first word gets the previous run's last bits from the
+//     metadata's warp tail (the run before in the tile, or the last run of
 //     the tile before);
 //   - a lane's partial last word belongs to the next lane (or warp), except
 //     at the end of the record, where it is written zero-padded;
 //   - the warp copies its words out with 16-byte stores.
-// No word is written twice and the output needs no clearing.
-constexpr uint32_t kWarpStageWords = 520;  // 1024 codes of <= 16 bits, plus alignment
+// No word is written twice and the output needs no clearing.  Taking 64
+// symbols a lane halves the per-lane work that does not depend on the symbol
+// count (offsets, shuffles, the shared words, the copy-out).
+constexpr uint32_t kPackRuns = 2;                                  // summing-pass runs per lane
+constexpr uint32_t kPackSyms = kPackRuns * kEncSymPerThread;       // symbols per lane
+constexpr uint32_t kPackItems = kEncThreads / 32 / kPackRuns;      // warp items per tile
+constexpr uint32_t kWarpStageWords = kPackSyms * 32 * 16 / 32 + 8;  // codes of <= 16 bits, + alignment
 static_assert(kWarpStageWords * (kEncThreads / 32) <= (uint32_t)kEncStageWords + 4, "staging");
 
 static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
@@ -921,19 +931,19 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
   uint32_t* rec_words =
       reinterpret_cast<uint32_t*>(a.out + records_at(a.nb, a.B, a.flags, a.sub_S));
   uint32_t* stw = sh.stage + warp * kWarpStageWords;
-  const uint32_t items = (a.tile_end - a.tile_begin) * kWarps;
+  const uint32_t items = (a.tile_end - a.tile_begin) * kPackItems;
   for (uint32_t it = blockIdx.x * kWarps + warp; it < items; it += gridDim.x * kWarps) {
     // last tiles first: their input is still in L2 from the length-summing pass
-    const uint32_t tile = a.tile_end - 1 - it / kWarps;
-    const uint32_t w = it % kWarps;
+    const uint32_t tile = a.tile_end - 1 - it / kPackItems;
+    const uint32_t v0 = (it % kPackItems) * kPackRuns;  // the item's first summing-pass run
     const uint32_t lo = tile * (uint32_t)kEncTile;
     const uint32_t hi = n - lo > (uint32_t)kEncTile ? lo + (uint32_t)kEncTile : n;
-    const uint32_t wlo = lo + w * 32 * kEncSymPerThread;
+    const uint32_t wlo = lo + v0 * 32 * kEncSymPerThread;
     if (wlo >= hi) continue;  // uniform: no symbol for this warp
-    const uint32_t g0 = wlo + lane * kEncSymPerThread;
-    const uint32_t cnt = g0 >= hi ? 0u : min(hi - g0, (uint32_t)kEncSymPerThread);
-    uint32_t x[kEncSymPerThread / 4];
-    load_symbols(a.in + g0, (int)cnt, x);
+    const uint32_t g0 = wlo + lane * kPackSyms;
+    const uint32_t cnt = g0 >= hi ? 0u : min(hi - g0, kPackSyms);
+    const uint32_t cnt0 = min(cnt, (uint32_t)kEncSymPerThread);  // symbols of my first run
+    const uint32_t cnt1 = cnt - cnt0;                            // and of my second
     const TileMeta& m = a.meta[tile];
     const bool starts = fast_mod(lo, a.fdB) == 0;
     const bool ends = fast_mod(hi, a.fdB) == 0 || hi == n;  // the tile ends its record
@@ -941,23 +951,27 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
     const uint32_t pre_b = a.tiles[tile].pre_b;
     const uint64_t O1 = starts ? pre_O + 1 + ceil32(pre_b) : pre_O;  // the record's delimiter
     const uint32_t b0 = starts ? 0u : pre_b;
-    // my bit position: the tile's start in its record, the warp's prefix, my lanes' prefix
-    const uint32_t c = cnt ? m.lane_bits[w * 32 + lane] : 0u;
+    // my runs' bit counts: lane_bits[32 v + j] of runs j = 2l, 2l + 1 of the
+    // item (v = v0 + l / 16), two adjacent u16 (a run without symbols may not
+    // have been written)
+    const uint32_t bb = cnt ? reinterpret_cast<const uint32_t*>(m.lane_bits)[v0 * 16 + lane] : 0u;
+    const uint32_t c0 = cnt0 ? (bb & 0xFFFFu) : 0u;
+    const uint32_t c = c0 + (cnt1 ? (bb >> 16) : 0u);
     uint32_t inc = c;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
       if (lane >= (uint32_t)d) inc += o;
     }
-    // bits of the tile's earlier warps: lane v < w loads warp v's count
-    const uint32_t wp = __reduce_add_sync(0xFFFFFFFFu, lane < w ? m.warp_bits[lane] : 0u);
+    // bits of the tile's earlier runs: lane v < v0 loads run v's count
+    const uint32_t wp = __reduce_add_sync(0xFFFFFFFFu, lane < v0 ? m.warp_bits[lane] : 0u);
     const uint32_t ws = b0 + wp;  // the warp's first payload bit
     const uint32_t we = ws + __shfl_sync(0xFFFFFFFFu, inc, 31);
     const uint32_t p = ws + inc - c;
     const uint32_t r = ws & 31u;
     // the last lane with symbols, and whether the record ends with it
-    const uint32_t last_lane = 31u - (__clz(__ballot_sync(0xFFFFFFFFu, cnt > 0)) );
-    const bool rec_end = ends && hi - wlo <= 32u * kEncSymPerThread;  // the warp holds the tile's end
+    const uint32_t last_lane = 31u - (__clz(__ballot_sync(0xFFFFFFFFu, cnt > 0)));
+    const bool rec_end = ends && hi - wlo <= 32u * kPackSyms;  // the warp holds the tile's end
     // staging: word index i of the payload goes to stw[i - wb + off], so that
     // 16-byte chunks of stw are 16-byte aligned in the output
     const uint32_t wb = ws >> 5;
@@ -982,16 +996,23 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
         nacc -= 32u;
       }
     };
-    if (cnt == kEncSymPerThread) {
+    // one 32-symbol run at g (k symbols of it)
+    auto pack_run = [&](uint32_t g, uint32_t k) {
+      uint32_t x[kEncSymPerThread / 4];
+      load_symbols(a.in + g, (int)k, x);
+      if (k == (uint32_t)kEncSymPerThread) {
 #pragma unroll
-      for (int j = 0; j < kEncSymPerThread / 2; ++j)
-        push(sh.lent[sym_of(x, 2 * j)], sh.lent[sym_of(x, 2 * j + 1)]);
-    } else {
+        for (int j = 0; j < kEncSymPerThread / 2; ++j)
+          push(sh.lent[sym_of(x, 2 * j)], sh.lent[sym_of(x, 2 * j + 1)]);
+      } else {
 #pragma unroll
-      for (int j = 0; j < kEncSymPerThread / 2; ++j)
-        push((uint32_t)(2 * j) < cnt ? sh.lent[sym_of(x, 2 * j)] : 0u,
-             (uint32_t)(2 * j + 1) < cnt ? sh.lent[sym_of(x, 2 * j + 1)] : 0u);
-    }
+        for (int j = 0; j < kEncSymPerThread / 2; ++j)
+          push((uint32_t)(2 * j) < k ? sh.lent[sym_of(x, 2 * j)] : 0u,
+               (uint32_t)(2 * j + 1) < k ? sh.lent[sym_of(x, 2 * j + 1)] : 0u);
+      }
+    };
+    if (cnt0) pack_run(g0, cnt0);
+    if (cnt1) pack_run(g0 + kEncSymPerThread, cnt1);
     const bool first = wi == w_first;  // no word completed
     // ---- the words shared with the lane before (or the warp before)
     const uint32_t tail = nacc ? acc_hi : 0u;  // my partial last word
@@ -999,7 +1020,7 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
     if (lane == 0) {
       prev = 0;
       if (r) {
-        const uint32_t t = w ? m.warp_tail[w - 1] : a.meta[tile - 1].warp_tail[kWarps - 1];
+        const uint32_t t = v0 ? m.warp_tail[v0 - 1] : a.meta[tile - 1].warp_tail[kWarps - 1];
         prev = (t & ((1u << r) - 1u)) << (32u - r);
       }
     }
@@ -1013,9 +1034,12 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
       pay[-1] = p + c;  // rec_words[O1]: the record's bit count
       if ((a.flags & kFlagSub) && hi == n) put_sub_tail(a, p + c);
     }
-    if (starts && w == 0 && lane == 0 && (a.flags & kFlagIndex))
+    if (starts && v0 == 0 && lane == 0 && (a.flags & kFlagIndex))
       reinterpret_cast<uint32_t*>(a.out + kHeaderBytes)[fast_div(lo, a.fdB)] = (uint32_t)O1;
-    if ((a.flags & kFlagSub) && cnt) put_sub_entry(a, g0, p);
+    if (a.flags & kFlagSub) {  // each run's first symbol may start a sub-block
+      if (cnt0) put_sub_entry(a, g0, p);
+      if (cnt1) put_sub_entry(a, g0 + kEncSymPerThread, p + c0);
+    }
     __syncwarp();
     // ---- copy out: payload words [wb, wend); the partial last word only at the record's end
     const uint32_t wend = (we >> 5) + ((rec_end && (we & 31u)) ? 1u : 0u);
