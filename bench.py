@@ -49,23 +49,35 @@ WORKLOADS = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # ncu captures on the 256 MiB profiling case, scaled by the units processed to a
 # 1 GiB launch (profiles/*.md).  Each figure holds only for the kernel sources
-# it was measured on: "digest" is kernel_digest() of those sources, and the
-# line reports null traffic when the sources have changed since.
-NCU_TRAFFIC = {"mixed-1GiB": {"digest": "e94e2e4bb67846ab", "sub_block": 2048,
-                              "decode": 4 * (232816640 + 235328256),
-                              "encode_pack": 4 * (288559872 + 167100928)}}
+# it was measured on: "digest" is kernel_digest(kernel) of the files that
+# kernel is compiled from, and the line reports null traffic when they have
+# changed since.
+NCU_TRAFFIC = {"mixed-1GiB": {"sub_block": 2048,
+                              "decode": {"digest": None, "bytes": None},
+                              "encode_pack": {"digest": None, "bytes": None}}}
+# the files each kernel is compiled from (its translation unit and headers)
+KERNEL_SOURCES = {
+    "decode": ["hz_decode.cu", "hz_decode_dev.cuh", "hz_internal.cuh", "../../include/hz.h"],
+    "encode_pack": ["hz_encode.cu", "hz_encode_dev.cuh", "hz_internal.cuh",
+                    "../../include/hz.h"],
+    "encode_summary": ["hz_encode.cu", "hz_encode_dev.cuh", "hz_internal.cuh",
+                       "../../include/hz.h"],
+    "histogram": ["hz_hist.cu", "hz_hist_dev.cuh", "hz_internal.cuh", "../../include/hz.h"],
+}
 
 
-def kernel_digest() -> str:
-    """SHA-256 (first 16 hex digits) over the CUDA sources of the library."""
+def kernel_digest(kernel=None) -> str:
+    """SHA-256 (first 16 hex digits) over the CUDA sources `kernel` is compiled
+    from (KERNEL_SOURCES), or over all of the library's CUDA sources."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1107_1525_gb300", "csrc")
+    files = KERNEL_SOURCES.get(kernel) or sorted(
+        f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -805,9 +817,10 @@ def run_gpu(args, world, rank, local, pg):
                "encode_gbs": o["encode_gbs"], "decode_gbs": o["decode_gbs"],
                "single_thread": cb["single_thread"]}
     stamp = NCU_TRAFFIC.get(args.workload, {})
-    digest = kernel_digest()
-    fresh = stamp.get("digest") == digest and stamp.get("sub_block", 0) == S
-    traffic = stamp.get(dom) if fresh else None
+    digest = kernel_digest(dom)
+    kstamp = stamp.get(dom) or {}
+    fresh = kstamp.get("digest") == digest and stamp.get("sub_block", 0) == S
+    traffic = kstamp.get("bytes") if fresh else None
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
