@@ -80,7 +80,10 @@ constexpr int kMaxScanCtas = (int)((1ull << 32) / kEncTile / kScanTilesPerCta); 
 struct DevState {
   uint32_t error;           // first error recorded (as -hz_status), 0 = none
   uint32_t error_where;     // kernel-specific detail for debugging
-  uint32_t pad0[2];
+  // the sub-block decoder's work tickets (groups of 32 sub-blocks handed out
+  // after each warp's first) and its count of finished CTAs: zero between
+  // launches, the launch's last CTA puts both back to zero
+  uint32_t dec_ticket, dec_done;
   // ---- cleared before every compress (one memset from here to `codes`)
   uint32_t tile_counter;    // ticket of the scan CTAs
   uint32_t enc_ok;          // set by the encoder's scan: 1 when the stream fits the output
