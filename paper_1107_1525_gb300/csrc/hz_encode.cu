@@ -14,7 +14,10 @@
 //      tile's start state (word position of the open record, bits already in
 //      it), fixes the stream size and checks it against the output capacity;
 //   3. encode_pack_kernel -- every tile is packed independently from its
-//      start state: each thread packs 32 consecutive symbols MSB-first with a
+//      start state (when every tile lies inside one record and no code is
+//      longer than 32 bits, warps pack 2048-symbol items on their own from
+//      the summing pass's per-thread bit counts: pack_warps_fast; otherwise
+//      per tile): each thread packs 32 consecutive symbols MSB-first with a
 //      64-bit shift accumulator (two codes per step when codes have at most
 //      16 bits), the tile's words are staged in shared memory (atomicOr only
 //      for a word split between two threads) and written out with 16-byte
@@ -213,10 +216,12 @@ __global__ void __launch_bounds__(kEncThreads, 4) encode_pack_kernel(EncodeArgs 
   const uint32_t maxlen = a.st->codes.maxlen;
   pack_load_tables(sh, a);
   __syncthreads();
-  // every tile inside one record and codes of at most 16 bits: warps pack on
-  // their own, from the tile metadata of the length-summing pass
+  // every tile inside one record and codes of at most 32 bits: warps pack on
+  // their own, from the tile metadata of the length-summing pass (two codes
+  // a step when no code is longer than 16 bits)
   if (warp_path(a.meta, a.B, maxlen)) {
-    pack_warps_fast(sh);
+    if (maxlen <= 16) pack_warps_fast<false>(sh);
+    else pack_warps_fast<true>(sh);
     return;
   }
   for (uint32_t i = blockIdx.x; i < a.tile_end - a.tile_begin; i += gridDim.x) {

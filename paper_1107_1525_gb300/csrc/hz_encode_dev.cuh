@@ -166,7 +166,7 @@ static __device__ __forceinline__ void load_tile_symbols(const EncodeArgs& a, ui
 // so that 32 lanes' lookups are one shared-memory wavefront, as the
 // histogram's counters are; s_code: right-aligned codes; s_sym: 32 bytes of
 // per-warp scratch.
-constexpr uint32_t kLenNoCode = 1u << 16;  // > 32 codes of at most 16 bits
+constexpr uint32_t kLenNoCode = 1u << 16;  // > 32 codes of at most 32 bits
 static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const uint32_t* s_len32,
                                                    const uint32_t* s_code, uint8_t* s_sym,
                                                    bool& bad) {
@@ -425,6 +425,7 @@ struct PackShared {
   EncodeArgs a;         // the launch arguments, read by the per-tile functions
   uint32_t entry[256];  // code << 6 | len, valid for codes of up to 26 bits
   uint32_t lent[256];   // code << (32 - len) | len, valid for codes of up to 16 bits
+  uint2 cl[256];        // {code << (32 - len), len}, valid for codes of up to 32 bits
   uint32_t len[256];
   uint32_t code_lo[256];
   uint32_t code_hi[256];
@@ -917,12 +918,18 @@ __device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, co
 // No word is written twice and the output needs no clearing.  Taking 64
 // symbols a lane halves the per-lane work that does not depend on the symbol
 // count (offsets, shuffles, the shared words, the copy-out).
+// kWide (codes of 17 to 32 bits): one code per step, from sh.cl.  A warp's
+// words may then not fit its staging area (2048 codes of 32 bits are 2048
+// words): such an item is written straight to the output instead, each lane
+// storing the words it completes and, last, its first word with the bits of
+// the lane before.
 constexpr uint32_t kPackRuns = 2;                                  // summing-pass runs per lane
 constexpr uint32_t kPackSyms = kPackRuns * kEncSymPerThread;       // symbols per lane
 constexpr uint32_t kPackItems = kEncThreads / 32 / kPackRuns;      // warp items per tile
 constexpr uint32_t kWarpStageWords = kPackSyms * 32 * 16 / 32 + 8;  // codes of <= 16 bits, + alignment
 static_assert(kWarpStageWords * (kEncThreads / 32) <= (uint32_t)kEncStageWords + 4, "staging");
 
+template <bool kWide>
 static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
   const EncodeArgs& a = sh.a;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -983,6 +990,32 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
     const uint32_t w_first = (p >> 5) - wb + off;
     uint32_t wi = w_first;
     const bool shared_head = (p & 31u) != 0 && c != 0;
+    // ---- copy-out range: payload words [wb, wend); the partial last word
+    // only at the record's end
+    const uint32_t wend = (we >> 5) + ((rec_end && (we & 31u)) ? 1u : 0u);
+    const uint32_t nw = wend - wb;
+    uint32_t* gbase = pay + wb - off;  // 16-byte aligned
+    // (uniform) the item's words do not fit the staging area: straight out
+    const bool direct = kWide && nw + off > kWarpStageWords;
+    uint32_t fw = 0;  // direct: my first completed word, stored last
+    auto emit = [&](uint32_t v) {
+      if (!kWide || !direct) stw[wi] = v;
+      else if (wi == w_first) fw = v;
+      else gbase[wi] = v;
+      ++wi;
+    };
+    // one code of up to 32 bits, left-aligned in c
+    auto push1 = [&](uint32_t cc, uint32_t l) {
+      acc_hi |= cc >> nacc;
+      acc_lo |= __funnelshift_r(0u, cc, nacc);  // cc << (32 - nacc), 0 for nacc = 0
+      nacc += l;
+      if (nacc >= 32u) {
+        emit(acc_hi);
+        acc_hi = acc_lo;
+        acc_lo = 0;
+        nacc -= 32u;
+      }
+    };
     auto push = [&](uint32_t ea, uint32_t eb) {
       const uint32_t la = ea & 31u;
       const uint32_t cw = (ea & ~31u) | __funnelshift_rc(eb & ~31u, 0u, la);  // (eb >> la)
@@ -990,7 +1023,7 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
       acc_lo |= __funnelshift_r(0u, cw, nacc);  // cw << (32 - nacc), 0 for nacc = 0
       nacc += la + (eb & 31u);
       if (nacc >= 32u) {
-        stw[wi++] = acc_hi;
+        emit(acc_hi);
         acc_hi = acc_lo;
         acc_lo = 0;
         nacc -= 32u;
@@ -1000,7 +1033,15 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
     auto pack_run = [&](uint32_t g, uint32_t k) {
       uint32_t x[kEncSymPerThread / 4];
       load_symbols(a.in + g, (int)k, x);
-      if (k == (uint32_t)kEncSymPerThread) {
+      if (kWide) {
+#pragma unroll
+        for (int j = 0; j < kEncSymPerThread; ++j) {
+          if (k == (uint32_t)kEncSymPerThread || (uint32_t)j < k) {
+            const uint2 e = sh.cl[sym_of(x, j)];
+            push1(e.x, e.y);
+          }
+        }
+      } else if (k == (uint32_t)kEncSymPerThread) {
 #pragma unroll
         for (int j = 0; j < kEncSymPerThread / 2; ++j)
           push(sh.lent[sym_of(x, 2 * j)], sh.lent[sym_of(x, 2 * j + 1)]);
@@ -1024,11 +1065,19 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
         prev = (t & ((1u << r) - 1u)) << (32u - r);
       }
     }
-    if (shared_head && !first) stw[w_first] |= prev;
+    if (kWide && direct) {
+      if (!first) gbase[w_first] = shared_head ? (fw | prev) : fw;
+    } else if (shared_head && !first) {
+      stw[w_first] |= prev;
+    }
     // a lane that completed no word keeps its bits, and the lane before's, in
     // `tail`: only the record's last lane can (a full lane holds >= 32 bits)
     const bool own_tail = lane == last_lane && rec_end;
-    if (own_tail && nacc) stw[wi] = first && shared_head ? (tail | prev) : tail;
+    if (own_tail && nacc) {
+      const uint32_t v = first && shared_head ? (tail | prev) : tail;
+      if (kWide && direct) gbase[wi] = v;
+      else stw[wi] = v;
+    }
     // ---- delimiter, index, sub-block offsets
     if (own_tail) {
       pay[-1] = p + c;  // rec_words[O1]: the record's bit count
@@ -1041,10 +1090,8 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
       if (cnt1) put_sub_entry(a, g0 + kEncSymPerThread, p + c0);
     }
     __syncwarp();
-    // ---- copy out: payload words [wb, wend); the partial last word only at the record's end
-    const uint32_t wend = (we >> 5) + ((rec_end && (we & 31u)) ? 1u : 0u);
-    const uint32_t nw = wend - wb;
-    uint32_t* gbase = pay + wb - off;  // 16-byte aligned
+    if (kWide && direct) continue;  // (uniform) already written
+    // ---- copy out
     for (uint32_t k = lane; 4 * k < nw + off; k += 32) {
       const uint32_t i0 = 4 * k;
       if (i0 >= off && i0 + 4 <= nw + off) {
@@ -1070,6 +1117,7 @@ static __device__ __forceinline__ void pack_load_tables(PackShared& sh, const En
     sh.code_hi[s] = (uint32_t)(c >> 32);
     sh.entry[s] = (uint32_t)(c << 6) | l;
     sh.lent[s] = (l && l <= 16) ? ((uint32_t)c << (32 - l)) | l : 0u;
+    sh.cl[s] = (l && l <= 32) ? make_uint2((uint32_t)(c << (32 - l)), l) : make_uint2(0u, 0u);
   }
   if (threadIdx.x == 0) sh.a = a;
 }

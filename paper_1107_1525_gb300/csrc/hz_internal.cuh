@@ -56,10 +56,10 @@ struct TileStatus {
 };
 
 // What the length-summing pass records about a tile when every tile lies
-// inside one record and no code is longer than 16 bits (the warp-parallel
+// inside one record and no code is longer than 32 bits (the warp-parallel
 // path): each thread's payload bits (its 32 symbols), each warp's bits, and
-// each warp's last 32 code bits (the bits the next warp's first word
-// continues).  The tile scan sums the warps' bits.
+// the last 32 code bits of the odd warps' runs (the bits the next packing
+// item's first word continues).  The tile scan sums the warps' bits.
 struct TileMeta {
   uint16_t lane_bits[kEncThreads];
   uint32_t warp_bits[kEncThreads / 32];
@@ -69,7 +69,7 @@ struct TileMeta {
 // The warp-parallel path's condition, the same in every encoder kernel.
 __host__ __device__ __forceinline__ bool warp_path(const TileMeta* meta, uint32_t B,
                                                    uint32_t maxlen) {
-  return meta != nullptr && B % (uint32_t)kEncTile == 0 && maxlen <= 16;
+  return meta != nullptr && B % (uint32_t)kEncTile == 0 && maxlen <= 32;
 }
 
 // The encoder's tile scan runs in CTAs of kScanTilesPerCta tiles; n < 2^32
@@ -227,7 +227,7 @@ struct EncodeArgs {
   uint32_t spin_limit;      // polls of the scan's look-back before it gives up
   // per-tile metadata for the warp-parallel packing path (null: not used);
   // written by the length-summing pass for tiles inside one record when no
-  // code is longer than 16 bits
+  // code is longer than 32 bits
   TileMeta* meta;
 };
 

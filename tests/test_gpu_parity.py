@@ -172,6 +172,36 @@ def test_tile_start_inside_a_code_longer_than_26_bits(hz, ctx):
         _check_round_trip(hz, ctx, x, B, lengths=lens)
 
 
+@pytest.mark.parametrize("maxlen", [17, 24, 32])
+@pytest.mark.parametrize("B,sub", [(8192, 0), (65536, 0), (65536, 2048)])
+def test_warp_path_codes_of_17_to_32_bits(hz, maxlen, B, sub):
+    """Blocks that are whole tiles and codes of 17 to 32 bits take the warp
+    packer one code a step.  A run of the longest codes overflows a warp's
+    staging area (2048 codes of more than 16 bits), so those items are
+    written straight to the output; the other runs (short codes, a mix) go
+    through the staging area.  Streams equal the oracle's byte for byte, with
+    and without sub-block offsets."""
+    lens = np.zeros(256, dtype=np.uint8)
+    lens[:maxlen] = np.arange(1, maxlen + 1)
+    lens[maxlen] = maxlen  # the chain 1, 2, ..., maxlen, maxlen is complete
+    rng = np.random.default_rng(maxlen * 7 + B)
+    parts = [rng.integers(0, 4, 3 * 8192 + 111),                   # short codes
+             rng.integers(maxlen - 1, maxlen + 1, 5 * 8192 + 5),   # the longest codes
+             rng.integers(maxlen // 2, maxlen + 1, 4 * 8192 + 77)]  # a mix
+    x = np.concatenate(parts).astype(np.uint8)
+    xd = torch.from_numpy(x).to(DEV)
+    codes = hz.make_codes(lens, oracle.canonical_codes(lens))
+    c = hz.Context(0)
+    c.set_option(hz.HZ_OPT_SUB_BLOCK, sub)
+    s = hz.compress(xd, B, ctx=c, codes=codes)
+    want = oracle.compress(x, B, lengths=lens, sub=sub)
+    got = s.cpu().numpy()
+    assert got.size == want.size and np.array_equal(got, want), (maxlen, B, sub)
+    st, y = _gpu_decompress(hz, c, s)
+    assert st == 0 and np.array_equal(y.cpu().numpy(), x)
+    c.close()
+
+
 def test_no_index_mode(hz, ctx):
     x = _zipf(500_000, 1.2, 9)
     _check_round_trip(hz, ctx, x, 4096, index=False)
