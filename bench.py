@@ -35,14 +35,18 @@ MiB = 1 << 20
 GiB = 1 << 30
 METRIC = "Huffman enc/dec GB/s of input, % of HBM peak; batch p50/p99 latency vs plain"
 WORKLOADS = {
-    "mixed-1GiB": dict(n=GiB, segment=64 * MiB, block=65536,
+    # sub: symbols per sub-block of the stored sub-block offsets, the size
+    # HZ_SUB_BLOCK_AUTO picks for the workload on a 152-SM GB300 (0: the
+    # paper's layout)
+    "mixed-1GiB": dict(n=GiB, segment=64 * MiB, block=65536, sub=2048,
                        desc="1 GiB uint8 in 64 MiB segments cycling Zipf(1.1) / geometric(0.3) "
                             "clipped to 255 / uniform-256 / uniform-16, 64 KiB blocks"),
-    "mixed-256MiB": dict(n=256 * MiB, segment=64 * MiB, block=65536,
+    "mixed-256MiB": dict(n=256 * MiB, segment=64 * MiB, block=65536, sub=2048,
                          desc="256 MiB: one 64 MiB segment of each kind of the 1 GiB mix, "
                               "64 KiB blocks (profiling case)"),
-    "zipf-1MiB": dict(n=MiB, block=4096, desc="1 MiB i.i.d. Zipf(1.1) bytes, 4 KiB blocks"),
-    "field-256MiB": dict(n=1 << 28, block=16384,
+    "zipf-1MiB": dict(n=MiB, block=4096, sub=0,
+                      desc="1 MiB i.i.d. Zipf(1.1) bytes, 4 KiB blocks"),
+    "field-256MiB": dict(n=1 << 28, block=16384, sub=512,
                          desc="2^28 int8 residuals of a smooth 512x512x1024 Gaussian field, "
                               "16 KiB blocks"),
 }
@@ -79,6 +83,11 @@ def kernel_digest(kernel=None) -> str:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def sub_block_of(args) -> int:
+    """The sub-block size of the run: --sub-block, else the workload's."""
+    return args.sub_block if args.sub_block is not None else WORKLOADS[args.workload]["sub"]
 
 
 def load_peaks():
@@ -255,7 +264,8 @@ def run_reference(args, world, rank, pg):
     import oracle
     sample = args.ref_sample_mib * MiB
     x, B = oracle_sample(args.workload, sample)
-    S = args.sub_block if B % max(args.sub_block, 1) == 0 else 0
+    S = sub_block_of(args)
+    S = S if B % max(S, 1) == 0 else 0
     for _ in range(args.warmup):
         time_oracle(x, B, 1, sub=S, threads=0)
     t_enc, t_dec, slen = time_oracle(x, B, args.steps, sub=S, threads=0)
@@ -651,7 +661,7 @@ def run_gpu(args, world, rank, local, pg):
     torch.cuda.set_device(dev)
     w = WORKLOADS[args.workload]
     B = w["block"]
-    S = args.sub_block
+    S = sub_block_of(args)
     x = make_input(args.workload, dev)
     n = x.numel()
     ctx = hz.Context(local)
@@ -864,9 +874,10 @@ def main():
     ap.add_argument("--impl", default="hz", choices=["hz", "reference"])
     ap.add_argument("--workload", default="mixed-1GiB", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--sub-block", type=int, default=2048,
+    ap.add_argument("--sub-block", type=int, default=None,
                     help="symbols per sub-block of the stored sub-block offsets (0 = the "
-                         "paper's layout with the block index only)")
+                         "paper's layout with the block index only; default: the "
+                         "workload's)")
     ap.add_argument("--ref-sample-mib", type=int, default=128,
                     help="per-step host sample of the reference (oracle) arm")
     ap.add_argument("--cpu-sample-mib", type=int, default=256,

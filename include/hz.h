@@ -222,7 +222,15 @@ hz_status hz_compress_noalloc(const uint8_t* d_in, uint64_t n, uint32_t block_si
                                  sub-block offsets of every S symbols (flags bit 1)
                                  when S divides the block size and the index is on;
                                  S a multiple of 32.  0 (default): the paper's layout
-                                 with the block index only.  Decoders accept either. */
+                                 with the block index only.  HZ_SUB_BLOCK_AUTO: S is
+                                 picked per call from n, the block size and the
+                                 device: the largest of 4096 .. 512 that divides the
+                                 block size and gives at least four sub-blocks per
+                                 decoder lane the device keeps resident (SMs x 768),
+                                 else 512 if that gives at least one per lane, else
+                                 none (the paper's layout).  Decoders accept any
+                                 layout. */
+#define HZ_SUB_BLOCK_AUTO 1
 #define HZ_OPT_SPIN_LIMIT 9   /* polls the encoder's look-back scan makes while waiting
                                  for a predecessor before it records HZ_ERR_TIMEOUT and
                                  returns (1 .. 2^24, default 2^20; each poll sleeps

@@ -246,13 +246,35 @@ uint64_t hz_compress_bound(uint64_t n, uint32_t block_size) {
   return kHeaderBytes + 4 * nb + 12 * nb + 4 * ((n + 3) / 4);
 }
 
+constexpr uint32_t kSubAuto = HZ_SUB_BLOCK_AUTO;
+
+// The sub-block size S a compression of n bytes in blocks of B writes (0:
+// none).  HZ_OPT_SUB_BLOCK = 1 picks it: the largest of 4096, 2048, 1024 and
+// 512 that divides B and leaves at least four sub-blocks for every lane the
+// sub-block decoder keeps resident (three CTAs of 256 threads per SM).  A
+// lane decodes a sub-block in one chain of dependent steps, so the launch
+// takes at least one sub-block's time after the last full round; with four
+// or more rounds that tail stays small.  Below that, 512 (the stream grows
+// by at most 1 %) while there is at least one sub-block of 512 per lane;
+// shorter streams keep the paper's layout, whose decoder splits every block
+// over a warp's 32 lanes and so has more parallel work to give them.
+static uint32_t resolve_sub(const hz_ctx* c, uint64_t n, uint32_t B) {
+  if (!c->opt_index || !c->opt_sub) return 0;
+  if (c->opt_sub != kSubAuto) return sub_size_ok(B, c->opt_sub) ? c->opt_sub : 0u;
+  const uint64_t lanes = (uint64_t)c->num_sms * 3 * 256;
+  for (uint32_t S = 4096; S >= 512; S /= 2)
+    if (sub_size_ok(B, S) && n / S >= 4 * lanes) return S;
+  return sub_size_ok(B, 512) && n / 512 >= lanes ? 512u : 0u;
+}
+
 uint64_t hz_compress_bound_ctx(hz_ctx* c, uint64_t n, uint32_t block_size) {
   if (!c || n > 0xFFFFFFFFull) return 0;
   const uint32_t B = block_size ? block_size : autotuned_block(c, n);
   uint64_t bound = hz_compress_bound(n, B);
-  if (c->opt_index && c->opt_sub && sub_size_ok(B, c->opt_sub)) {
+  const uint32_t S = resolve_sub(c, n, B);
+  if (S) {
     const uint64_t nb = (n + B - 1) / B;
-    bound += 4 + 4 * nb * (B / c->opt_sub - 1);
+    bound += 4 + 4 * nb * (B / S - 1);
   }
   return bound;
 }
@@ -281,7 +303,8 @@ hz_status hz_set_option(hz_ctx* c, int key, int64_t v) {
       c->opt_tune_batched = (int)v;
       return HZ_OK;
     case HZ_OPT_SUB_BLOCK:
-      if (v != 0 && (v < 32 || v % 32 != 0 || v > (int64_t)kMaxBlock)) return HZ_ERR_ARG;
+      if (v != 0 && v != kSubAuto && (v < 32 || v % 32 != 0 || v > (int64_t)kMaxBlock))
+        return HZ_ERR_ARG;
       c->opt_sub = (uint32_t)v;
       return HZ_OK;
     case HZ_OPT_DECODE_LUT_BITS:
@@ -477,11 +500,11 @@ static hz_status encode_setup(hz_ctx* c, const uint8_t* d_in, uint64_t n, uint32
   a->nb = (uint32_t)((n + B - 1) / B);
   a->flags = c->opt_index ? kFlagIndex : 0;
   // sub-block offsets when asked for and S suits B (they need the index)
-  const bool sub = c->opt_index && c->opt_sub && sub_size_ok(B, c->opt_sub);
-  if (sub) a->flags |= kFlagSub;
-  a->sub_S = sub ? c->opt_sub : 0;
-  a->sub_M = sub ? B / c->opt_sub : 1;
-  a->fdS = make_fastdiv(sub ? c->opt_sub : 1);
+  const uint32_t S = resolve_sub(c, n, B);
+  if (S) a->flags |= kFlagSub;
+  a->sub_S = S;
+  a->sub_M = S ? B / S : 1;
+  a->fdS = make_fastdiv(S ? S : 1);
   a->spin_limit = c->opt_spin_limit;
   a->meta = c->d_meta;
   a->out = d_out;

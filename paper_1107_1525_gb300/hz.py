@@ -26,6 +26,7 @@ HZ_OPT_INDEX, HZ_OPT_PROFILE, HZ_OPT_DECODE_LUT_BITS = 1, 2, 3
 HZ_OPT_DECODE_THREADS, HZ_OPT_AUTOTUNE, HZ_OPT_BATCH_PLAIN = 4, 5, 6
 HZ_OPT_BATCH_MAX_REQS, HZ_OPT_SUB_BLOCK = 7, 8
 HZ_OPT_SPIN_LIMIT, HZ_OPT_INJECT_SCAN_STALL, HZ_OPT_TUNE_BATCHED = 9, 10, 11
+HZ_SUB_BLOCK_AUTO = 1  # HZ_OPT_SUB_BLOCK value: S picked per call
 HZ_OP_COMPRESS, HZ_OP_DECOMPRESS = 0, 1
 
 # the C symbols include/hz.h declares (checked by the test suite)

@@ -105,7 +105,7 @@ def test_sub_block_cta_widths(hz, threads):
 def test_sub_block_option_values(hz):
     ctx = hz.Context(0)
     assert ctx.get_option(hz.HZ_OPT_SUB_BLOCK) == 0
-    for bad in (1, 16, 48, 100, (1 << 24) + 32):
+    for bad in (2, 16, 48, 100, (1 << 24) + 32):
         with pytest.raises(hz.HzError):
             ctx.set_option(hz.HZ_OPT_SUB_BLOCK, bad)
     # an S that does not divide B leaves the stream in the paper's layout
@@ -123,6 +123,45 @@ def test_sub_block_option_values(hz):
     assert hz.hz_sync(ctx) == 0
     got = out[: int(ol.item())].cpu().numpy()
     assert np.array_equal(got, oracle.compress(x.cpu().numpy(), 4096, index=False))
+    ctx.close()
+
+
+def test_sub_block_automatic_size(hz):
+    """HZ_SUB_BLOCK_AUTO: the largest S of 4096 .. 512 dividing B that leaves
+    four sub-blocks for each of the decoder's resident lanes (SMs x 768), else
+    512 when that leaves at least one, else none.  The choice is read back
+    from the capacity bound (which counts the offsets) and from a stream,
+    which must be the oracle's for that S."""
+    ctx = _ctx(hz, hz.HZ_SUB_BLOCK_AUTO)
+    assert ctx.get_option(hz.HZ_OPT_SUB_BLOCK) == hz.HZ_SUB_BLOCK_AUTO
+    lanes = torch.cuda.get_device_properties(0).multi_processor_count * 768
+
+    def want(n, B):
+        for S in (4096, 2048, 1024, 512):
+            if B % S == 0 and n // S >= 4 * lanes:
+                return S
+        return 512 if B % 512 == 0 and n // 512 >= lanes else 0
+
+    def chosen(n, B):
+        extra = hz.hz_compress_bound_ctx(ctx, n, B) - hz.hz_compress_bound(n, B)
+        if extra == 0:
+            return 0
+        nb = -(-n // B)
+        per_block = (extra - 4) // (4 * nb)  # B / S - 1
+        return B // (per_block + 1)
+
+    for n, B in ((MiB, 4096), (lanes * 512, 4096), (lanes * 512 - 1, 4096),
+                 (2 * lanes * 512, 256), (4 * lanes * 512, 65536),
+                 (4 * lanes * 1024 + 5, 65536), (4 * lanes * 2048, 16384),
+                 (4 * lanes * 4096 - 1, 65536), (4 * lanes * 2048, 65536 * 3)):
+        assert chosen(n, B) == want(n, B), (n, B)
+    # a stream at the smallest size that gets S = 512, and one just below it
+    for n, S in ((lanes * 512, 512), (MiB, 0)):
+        x = datagen.zipf_buffer(n, s=1.1, seed=12, device=DEV)
+        s = hz.compress(x, 4096, ctx=ctx)
+        assert np.array_equal(s.cpu().numpy(), oracle.compress(x.cpu().numpy(), 4096, sub=S))
+        st, y = _decode(hz, ctx, s, n)
+        assert st == 0 and torch.equal(y, x)
     ctx.close()
 
 
