@@ -637,12 +637,18 @@ struct RingWin {
     return fast_smem_words()[ring_w + i % kRingWords];
   }
   __device__ __forceinline__ void request(uint32_t h) {
-    const uint32_t bytes = h < full_slots ? 32u : (h == full_slots ? tail_bytes : 0u);
-    const uint32_t b0 = bytes < 16 ? bytes : 16u, b1 = bytes > 16 ? bytes - 16 : 0u;
     const uint8_t* src = abase + 32ull * h;
     const uint32_t dst = ring_s + 32 * (h % kRingSlots);
-    cp_async16(dst, b0 ? src : abase, b0);
-    cp_async16(dst + 16, b1 ? src + 16 : abase, b1);
+    if (h < full_slots) {  // a slot wholly inside the stream buffer (all but the last)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16), "l"(src + 16)
+                   : "memory");
+    } else {  // the buffer's last bytes, zero-filled past its end
+      const uint32_t bytes = h == full_slots ? tail_bytes : 0u;
+      const uint32_t b0 = bytes < 16 ? bytes : 16u, b1 = bytes > 16 ? bytes - 16 : 0u;
+      cp_async16(dst, b0 ? src : abase, b0);
+      cp_async16(dst + 16, b1 ? src + 16 : abase, b1);
+    }
     cp_async_commit();
   }
   // Start at payload bit `pos`.  kLongSteps (steps of up to 32 bits, decoder
