@@ -81,6 +81,8 @@ __global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs 
 
 __global__ void __launch_bounds__(kScanThreads) encode_scan_kernel(EncodeArgs a) {
   __shared__ Summary s_warp[kScanThreads / 32];
+  __shared__ Summary s_wpre[kScanThreads / 32];  // each warp's exclusive prefix in the CTA
+  __shared__ Summary s_agg;                      // the CTA's aggregate
   __shared__ uint32_t s_cta;
   __shared__ ScanState s_excl;
   __shared__ int s_abort;
@@ -114,12 +116,23 @@ __global__ void __launch_bounds__(kScanThreads) encode_scan_kernel(EncodeArgs a)
   if (lane == 0) ex = Summary{0, 0, 0, 0};
   if (lane == 31) s_warp[warp] = inc;
   __syncthreads();
-  Summary wpre{0, 0, 0, 0}, cta_agg{0, 0, 0, 0};
-  for (int w = 0; w < kScanThreads / 32; ++w) {
-    if (w < warp) wpre = combine(wpre, s_warp[w]);
-    cta_agg = combine(cta_agg, s_warp[w]);
+  // warp 0 scans the warps' aggregates: each warp's prefix and the CTA's total
+  if (warp == 0) {
+    const Summary v = lane < kScanThreads / 32 ? s_warp[lane] : Summary{0, 0, 0, 0};
+    Summary wi = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      Summary o = shfl_up_summary(wi, d);
+      if (lane >= d) wi = combine(o, wi);
+    }
+    Summary we = shfl_up_summary(wi, 1);
+    if (lane == 0) we = Summary{0, 0, 0, 0};
+    if (lane < kScanThreads / 32) s_wpre[lane] = we;
+    if (lane == 31) s_agg = wi;
   }
-  ex = combine(wpre, ex);
+  __syncthreads();
+  const Summary cta_agg = s_agg;
+  ex = combine(s_wpre[warp], ex);
 
   if (warp == 0) {
     TileStatus* aux = st->scan_aux;

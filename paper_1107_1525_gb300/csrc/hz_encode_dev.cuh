@@ -262,8 +262,11 @@ static __device__ __forceinline__ Summary meta_summary(const EncodeArgs& a, uint
   const uint32_t syms = n - lo > (uint32_t)kEncTile ? (uint32_t)kEncTile : n - lo;
   const uint32_t warps = (syms + 32 * kEncSymPerThread - 1) / (32 * kEncSymPerThread);
   uint32_t total = 0;  // (warps past the input's end hold no symbol and write nothing)
+  const uint4 v0 = *reinterpret_cast<const uint4*>(&m.warp_bits[0]);
+  const uint4 v1 = *reinterpret_cast<const uint4*>(&m.warp_bits[4]);
+  const uint32_t wb[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-  for (uint32_t w = 0; w < kEncThreads / 32; ++w) total += w < warps ? m.warp_bits[w] : 0u;
+  for (uint32_t w = 0; w < kEncThreads / 32; ++w) total += w < warps ? wb[w] : 0u;
   const bool starts = fast_mod(tile * (uint32_t)kEncTile, a.fdB) == 0;
   return starts ? Summary{1, 0, 0, total} : Summary{0, total, 0, 0};
 }
