@@ -1188,49 +1188,53 @@ __device__ __noinline__ void decode_block_warp0(const DecodeArgs& a, uint32_t k)
   {
     uint32_t rem = active ? v : 0u;
     uint8_t* dst = a.out + (uint64_t)k * sh.c.B + (inc - v);
+    auto step = [&]() -> uint32_t {
+      const uint32_t h = lut0_hi(sh, lut0_at<kRep>(w.bh, sW, c2));
+      w.take0(h);
+      return h;
+    };
     if (rem) {
       w.init0(start);
-      // bytes up to a 16-byte boundary (at most 15 steps: within the slots init awaited)
-      while (rem && (((uintptr_t)dst) & 15)) {
+      // bytes up to a 32-byte boundary, a refill point every 8 (a step reads at
+      // most 12 bits: 8 steps stay within the slots a refill awaits)
+      while (rem && (((uintptr_t)dst) & 31)) {
+        if ((((uintptr_t)dst) & 7) == 0) w.refill<false>();
         w.fill0();
-        const uint32_t h = lut0_hi(sh, lut0_at<kRep>(w.bh, sW, c2));
-        w.take0(h);
-        *dst++ = (uint8_t)(h >> 8);
+        *dst++ = (uint8_t)(step() >> 8);
         --rem;
       }
     }
-    // 16 symbols per 16-byte store, one refill point per 16 symbols
-    while (__any_sync(0xFFFFFFFFu, rem >= 16)) {
-      if (rem >= 16) {
-        w.refill<false>();
-        uint32_t q[4];
+    // 32 symbols per 32-byte store (one whole sector per write request), a
+    // refill point every 16 steps, a fill every K2 steps counted over the 32;
+    // four symbols into a word with three byte permutes
+    while (__any_sync(0xFFFFFFFFu, rem >= 32)) {
+      if (rem >= 32) {
+        uint32_t q[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          uint32_t word = 0;
+        for (int half = 0; half < 2; ++half) {
+          w.refill<false>();
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            if ((4 * j + b) % K2 == 0) w.fill0();
-            const uint32_t h = lut0_hi(sh, lut0_at<kRep>(w.bh, sW, c2));
-            w.take0(h);
-            // byte b of the word <- the symbol (byte 1 of h)
-            word = __byte_perm(word, h, b == 0 ? 0x3215u : b == 1 ? 0x3250u : b == 2 ? 0x3510u : 0x5210u);
+          for (int j = 0; j < 4; ++j) {
+            uint32_t h[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              if ((16 * half + 4 * j + b) % K2 == 0) w.fill0();
+              h[b] = step();
+            }
+            q[4 * half + j] = __byte_perm(__byte_perm(h[0], h[1], 0x0051u),
+                                          __byte_perm(h[2], h[3], 0x0051u), 0x5410u);
           }
-          q[j] = word;
         }
-        *reinterpret_cast<uint4*>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
-        dst += 16;
-        rem -= 16;
+        st_global_v8(dst, q);
+        dst += 32;
+        rem -= 32;
       }
     }
-    if (rem) {
-      w.refill<false>();
-      while (rem) {
-        w.fill0();
-        const uint32_t h = lut0_hi(sh, lut0_at<kRep>(w.bh, sW, c2));
-        w.take0(h);
-        *dst++ = (uint8_t)(h >> 8);
-        --rem;
-      }
+    for (uint32_t t = 0; rem; ++t) {  // a refill point every 8
+      if ((t & 7) == 0) w.refill<false>();
+      w.fill0();
+      *dst++ = (uint8_t)(step() >> 8);
+      --rem;
     }
     if (active && v) bad = w.pos0() != exit_;
   }
