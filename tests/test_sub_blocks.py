@@ -92,6 +92,37 @@ def test_sub_block_decoder_modes(hz, name, W):
     ctx.close()
 
 
+@pytest.mark.parametrize("maxlen", [11, 20, 28, 32])
+@pytest.mark.parametrize("B,S", [(65536, 2048), (16384, 512)])
+def test_sub_block_runs_of_long_codes(hz, maxlen, B, S):
+    """Complete codes with rare codes of over 10 bits (up to 32), in runs:
+    hundreds of the longest codes in a row, across refill points and
+    sub-block boundaries, at a sub-block's start and at the stream's end, so
+    that a lane's steps read far ahead in its ring."""
+    lengths = _chain(maxlen)
+    syms = np.nonzero(lengths)[0]
+    longest = syms[lengths[syms] == maxlen]
+    long_ish = syms[lengths[syms] > 10]
+    codes = hz.make_codes(lengths, oracle.canonical_codes(lengths))
+    ctx = _ctx(hz, S)
+    n = 5 * B + 3 * S + 777
+    x = _sample(lengths, n, maxlen + B)
+    rng = np.random.default_rng(maxlen)
+    for at, run in ((0, 300), (S - 100, 400), (2 * B + S, 2 * S), (n - 500, 500),
+                    (3 * B + 17, 33)):
+        x[at:at + run] = longest[rng.integers(0, len(longest), len(x[at:at + run]))]
+    x[rng.integers(0, n, 3000)] = long_ish[rng.integers(0, len(long_ish), 3000)]
+    xd = torch.from_numpy(x).to(DEV)
+    s = hz.compress(xd, B, ctx=ctx, codes=codes)
+    want = oracle.compress(x, B, lengths=lengths, sub=S)
+    assert np.array_equal(s.cpu().numpy(), want), (maxlen, B, S)
+    st, y = _decode(hz, ctx, s, n)
+    assert st == 0 and torch.equal(y, xd), (maxlen, B, S)
+    st, y = _decode(hz, ctx, torch.from_numpy(want).to(DEV), n)
+    assert st == 0 and torch.equal(y, xd)
+    ctx.close()
+
+
 @pytest.mark.parametrize("threads", [128, 256])
 def test_sub_block_cta_widths(hz, threads):
     ctx = _ctx(hz, 1024, HZ_OPT_DECODE_THREADS=threads)
