@@ -1193,8 +1193,8 @@ __device__ __noinline__ void decode_block_warp0(const DecodeArgs& a, uint32_t k)
       w.take0(h);
       return h;
     };
-    if (rem) {
-      w.init0(start);
+    if (rem) w.init0(start);
+    if (sh.c.B >= 65536) {  // uniform: long ranges (2048+ symbols a lane)
       // bytes up to a 32-byte boundary, a refill point every 8 (a step reads at
       // most 12 bits: 8 steps stay within the slots a refill awaits)
       while (rem && (((uintptr_t)dst) & 31)) {
@@ -1203,31 +1203,59 @@ __device__ __noinline__ void decode_block_warp0(const DecodeArgs& a, uint32_t k)
         *dst++ = (uint8_t)(step() >> 8);
         --rem;
       }
-    }
-    // 32 symbols per 32-byte store (one whole sector per write request), a
-    // refill point every 16 steps, a fill every K2 steps counted over the 32;
-    // four symbols into a word with three byte permutes
-    while (__any_sync(0xFFFFFFFFu, rem >= 32)) {
-      if (rem >= 32) {
-        uint32_t q[8];
+      // 32 symbols per 32-byte store (one whole sector per write request), a
+      // refill point every 16 steps, a fill every K2 steps counted over the 32;
+      // four symbols into a word with three byte permutes
+      while (__any_sync(0xFFFFFFFFu, rem >= 32)) {
+        if (rem >= 32) {
+          uint32_t q[8];
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
+          for (int half = 0; half < 2; ++half) {
+            w.refill<false>();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              uint32_t h[4];
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                if ((16 * half + 4 * j + b) % K2 == 0) w.fill0();
+                h[b] = step();
+              }
+              q[4 * half + j] = __byte_perm(__byte_perm(h[0], h[1], 0x0051u),
+                                            __byte_perm(h[2], h[3], 0x0051u), 0x5410u);
+            }
+          }
+          st_global_v8(dst, q);
+          dst += 32;
+          rem -= 32;
+        }
+      }
+    } else {  // short ranges: 16-byte stores, fewer single bytes at the ends
+      // bytes up to a 16-byte boundary (at most 15 steps: within the slots init awaited)
+      while (rem && (((uintptr_t)dst) & 15)) {
+        w.fill0();
+        *dst++ = (uint8_t)(step() >> 8);
+        --rem;
+      }
+      // 16 symbols per 16-byte store, one refill point per 16 symbols
+      while (__any_sync(0xFFFFFFFFu, rem >= 16)) {
+        if (rem >= 16) {
           w.refill<false>();
+          uint32_t q[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             uint32_t h[4];
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-              if ((16 * half + 4 * j + b) % K2 == 0) w.fill0();
+              if ((4 * j + b) % K2 == 0) w.fill0();
               h[b] = step();
             }
-            q[4 * half + j] = __byte_perm(__byte_perm(h[0], h[1], 0x0051u),
-                                          __byte_perm(h[2], h[3], 0x0051u), 0x5410u);
+            q[j] = __byte_perm(__byte_perm(h[0], h[1], 0x0051u),
+                               __byte_perm(h[2], h[3], 0x0051u), 0x5410u);
           }
+          *reinterpret_cast<uint4*>(dst) = make_uint4(q[0], q[1], q[2], q[3]);
+          dst += 16;
+          rem -= 16;
         }
-        st_global_v8(dst, q);
-        dst += 32;
-        rem -= 32;
       }
     }
     for (uint32_t t = 0; rem; ++t) {  // a refill point every 8
