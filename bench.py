@@ -57,8 +57,8 @@ WORKLOADS = {
 # kernel is compiled from, and the line reports null traffic when they have
 # changed since.
 NCU_TRAFFIC = {"mixed-1GiB": {"sub_block": 2048,
-                              "decode": {"digest": "0075b6c2b323c289",
-                                         "bytes": 4 * (231672064 + 233286912)},
+                              "decode": {"digest": "6c0abc3a8f67ef23",
+                                         "bytes": 4 * (231604736 + 233474560)},
                               "encode_pack": {"digest": "67633da78ac34a4a",
                                               "bytes": 4 * (288525056 + 167749376)}}}
 # the files each kernel is compiled from (its translation unit and headers)
@@ -774,6 +774,10 @@ def run_gpu(args, world, rank, local, pg):
     # ---- end to end: host (pinned) buffers through the C ABI, copies inside the timing
     h_in = torch.empty(n, dtype=torch.uint8, pin_memory=True)
     h_in.copy_(x.cpu())
+    # the input's digest: the generators are seeded, but the field goes through an
+    # FFT, whose last bits may differ between library versions
+    import hashlib
+    input_sha = hashlib.sha256(h_in.numpy().data).hexdigest()[:16]
     h_s = torch.empty(cap, dtype=torch.uint8, pin_memory=True)
     h_y = torch.empty(n, dtype=torch.uint8, pin_memory=True)
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
@@ -841,6 +845,7 @@ def run_gpu(args, world, rank, local, pg):
         "config": {"workload": args.workload, "desc": w["desc"], "n_bytes": n, "block_size": B,
                    "sub_block": S if flags & 2 else 0, "flags": flags,
                    "stream_bytes": stream_len, "ratio": stream_len / n,
+                   "input_sha256": input_sha,
                    "l2": "inputs larger than L2 (no flush needed)",
                    "step": "compress + decompress", "parallelism": f"replicas x{world}"},
         "encode_gbs": n / (enc_call_ms * 1e-3) / 1e9, "decode_gbs": n / (dec_call_ms * 1e-3) / 1e9,

@@ -22,7 +22,7 @@ struct ProfRec {
 
 // Host-buffer decompression of large streams with an index runs as a
 // pipeline of this many block groups (copy in, decode, copy out overlap).
-constexpr int kPipeGroups = 8;
+constexpr int kPipeGroups = 12;
 constexpr uint64_t kPipeMinBytes = 32ull << 20;
 // Streams without an index at least this long get the parallel chase.
 constexpr uint64_t kChaseParallelMin = 8ull << 20;
