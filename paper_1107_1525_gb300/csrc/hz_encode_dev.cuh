@@ -1019,17 +1019,20 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
         nacc -= 32u;
       }
     };
+    // Two codes of at most 16 bits a step.  The shifts take their amounts mod
+    // 32, so ea's and nacc's bits above the low five ride along: nacc's low six
+    // bits count the accumulator's bits (at most 31 + 32), and the codes' bits
+    // that ea + eb adds land above bit 15 (bits 5-15 of an entry are zero).
     auto push = [&](uint32_t ea, uint32_t eb) {
-      const uint32_t la = ea & 31u;
-      const uint32_t cw = (ea & ~31u) | __funnelshift_rc(eb & ~31u, 0u, la);  // (eb >> la)
-      acc_hi |= cw >> nacc;
+      const uint32_t cw = (ea & ~31u) | __funnelshift_r(eb & ~31u, 0u, ea);  // eb's code >> la
+      acc_hi |= __funnelshift_r(cw, 0u, nacc);  // cw >> nacc
       acc_lo |= __funnelshift_r(0u, cw, nacc);  // cw << (32 - nacc), 0 for nacc = 0
-      nacc += la + (eb & 31u);
-      if (nacc >= 32u) {
+      nacc += ea + eb;
+      if (nacc & 32u) {
         emit(acc_hi);
         acc_hi = acc_lo;
         acc_lo = 0;
-        nacc -= 32u;
+        nacc ^= 32u;
       }
     };
     // one 32-symbol run at g (k symbols of it)
@@ -1059,6 +1062,7 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
     if (cnt1) pack_run(g0 + kEncSymPerThread, cnt1);
     const bool first = wi == w_first;  // no word completed
     // ---- the words shared with the lane before (or the warp before)
+    nacc &= 31u;
     const uint32_t tail = nacc ? acc_hi : 0u;  // my partial last word
     uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, tail, 1);
     if (lane == 0) {
