@@ -409,9 +409,10 @@ static __device__ void scan_tiles_cta(const EncodeArgs& a, Summary* s_warp /* [3
 // at and writes the entry.
 static __device__ __forceinline__ void put_sub_entry(const EncodeArgs& a, uint32_t g,
                                                      uint32_t bit) {
+  if (fast_mod(g, a.fdS) != 0) return;  // (S divides B: not a boundary; the common case)
   const uint32_t k = fast_div(g, a.fdB);
   const uint32_t r = g - k * a.B;  // position in the block
-  if (r == 0 || fast_mod(r, a.fdS) != 0) return;
+  if (r == 0) return;  // a block start: no entry
   uint32_t* e = reinterpret_cast<uint32_t*>(a.out + sub_entries_at(a.nb));
   e[(uint64_t)k * (a.sub_M - 1) + fast_div(r, a.fdS) - 1] = bit;
 }
@@ -989,7 +990,7 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
     const uint32_t off = (uint32_t)(((uintptr_t)(pay + wb)) >> 2) & 3u;
     // ---- pack: every completed word goes to the staging area (a shared first
     // word too: the previous lane's bits are ORed into it below)
-    uint32_t acc_hi = 0, acc_lo = 0, nacc = p & 31u;
+    uint32_t acc_hi = 0, nacc = p & 31u;
     const uint32_t w_first = (p >> 5) - wb + off;
     uint32_t wi = w_first;
     const bool shared_head = (p & 31u) != 0 && c != 0;
@@ -1008,14 +1009,15 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
       ++wi;
     };
     // one code of up to 32 bits, left-aligned in c
+    // (what passes the word, cc << (32 - nacc), is non-zero only when the word
+    // completes: it becomes the next word's start)
     auto push1 = [&](uint32_t cc, uint32_t l) {
+      const uint32_t over = __funnelshift_r(0u, cc, nacc);  // 0 for nacc = 0
       acc_hi |= cc >> nacc;
-      acc_lo |= __funnelshift_r(0u, cc, nacc);  // cc << (32 - nacc), 0 for nacc = 0
       nacc += l;
       if (nacc >= 32u) {
         emit(acc_hi);
-        acc_hi = acc_lo;
-        acc_lo = 0;
+        acc_hi = over;
         nacc -= 32u;
       }
     };
@@ -1023,15 +1025,17 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
     // 32, so ea's and nacc's bits above the low five ride along: nacc's low six
     // bits count the accumulator's bits (at most 31 + 32), and the codes' bits
     // that ea + eb adds land above bit 15 (bits 5-15 of an entry are zero).
+    // The bits of the pair that pass the word (cw << (32 - nacc)) are non-zero
+    // only when the word completes, so they need no second accumulator: they
+    // become the next word's start.
     auto push = [&](uint32_t ea, uint32_t eb) {
       const uint32_t cw = (ea & ~31u) | __funnelshift_r(eb & ~31u, 0u, ea);  // eb's code >> la
-      acc_hi |= __funnelshift_r(cw, 0u, nacc);  // cw >> nacc
-      acc_lo |= __funnelshift_r(0u, cw, nacc);  // cw << (32 - nacc), 0 for nacc = 0
+      const uint32_t over = __funnelshift_r(0u, cw, nacc);  // cw << (32 - nacc), 0 for nacc = 0
+      acc_hi |= __funnelshift_r(cw, 0u, nacc);              // cw >> nacc
       nacc += ea + eb;
       if (nacc & 32u) {
         emit(acc_hi);
-        acc_hi = acc_lo;
-        acc_lo = 0;
+        acc_hi = over;
         nacc ^= 32u;
       }
     };
