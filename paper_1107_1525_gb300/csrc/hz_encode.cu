@@ -31,35 +31,11 @@
 
 namespace hz {
 
-__global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs a) {
-  __shared__ uint8_t s_len[256];  // 64 words: random lookups conflict at most 2-way
-  // warp-parallel path: the lengths once per lane in the lane's own bank, the
-  // right-aligned codes, 32 bytes of scratch per warp
-  extern __shared__ uint32_t s_len32[];  // 256 * 32 words (dynamic, that path only)
-  __shared__ uint32_t s_code[256];
-  __shared__ uint8_t s_sym[kEncThreads];
-  __shared__ uint32_t s_wsum[kEncThreads / 32];
-  __shared__ Summary s_warp[kEncThreads / 32];
-  const CodeTable* ct = &a.st->codes;
-  if (ct->maxlen > (uint32_t)kMaxLen) return;  // code construction failed; already reported
-  const bool warps = warp_path(a.meta, a.B, ct->maxlen);
-  for (int s = threadIdx.x; s < 256; s += kEncThreads) {
-    s_len[s] = ct->len[s];
-    s_code[s] = (uint32_t)ct->code[s];
-  }
-  if (warps) {
-    for (int i = threadIdx.x; i < 256 * 32; i += kEncThreads) {
-      const uint32_t l = ct->len[i >> 5];
-      s_len32[i] = l ? l : kLenNoCode;
-    }
-  }
-  __syncthreads();
+// The per-tile summaries (every path but the warp-parallel one), by the
+// first kEncThreads threads of the CTA.
+static __device__ __forceinline__ void summary_tiles(const EncodeArgs& a, const uint8_t* s_len,
+                                                     uint32_t* s_wsum, Summary* s_warp) {
   bool bad = false;
-  if (warps) {  // uniform
-    count_warps(a, s_len32, s_code, s_sym, bad);
-    if (bad) set_error(a.st, HZ_ERR_ARG, 0x200);
-    return;
-  }
   // the next tile's symbols are loaded while the current one is summarised
   uint32_t x[kEncSymPerThread / 4], xn[kEncSymPerThread / 4];
   uint32_t tile = blockIdx.x;
@@ -72,6 +48,51 @@ __global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs 
     for (int k = 0; k < kEncSymPerThread / 4; ++k) x[k] = xn[k];
   }
   if (bad) set_error(a.st, HZ_ERR_ARG, 0x200);  // a byte without a code (caller's code table)
+}
+
+// Streams whose blocks are not a whole number of tiles (or without the
+// metadata of the warp-parallel path): per-tile summaries.
+__global__ void __launch_bounds__(kEncThreads) encode_summary_kernel(EncodeArgs a) {
+  __shared__ uint8_t s_len[256];  // 64 words: random lookups conflict at most 2-way
+  __shared__ uint32_t s_wsum[kEncThreads / 32];
+  __shared__ Summary s_warp[kEncThreads / 32];
+  const CodeTable* ct = &a.st->codes;
+  if (ct->maxlen > (uint32_t)kMaxLen) return;  // code construction failed; already reported
+  for (int s = threadIdx.x; s < 256; s += kEncThreads) s_len[s] = ct->len[s];
+  __syncthreads();
+  summary_tiles(a, s_len, s_wsum, s_warp);
+}
+
+// Blocks of whole tiles with the warp-parallel path's metadata: the
+// warp-parallel summing pass when no code is longer than 32 bits (decided
+// here, from the code table), else the per-tile summaries by the CTA's first
+// kEncThreads threads (the others leave; the tile barrier counts kEncThreads).
+__global__ void __launch_bounds__(kSumWarpThreads, 3) encode_summary_warps_kernel(EncodeArgs a) {
+  extern __shared__ __align__(16) uint8_t s_tab[];  // kSumTabBytes (dynamic)
+  __shared__ uint8_t s_len[256];
+  __shared__ uint32_t s_code[256];
+  __shared__ uint8_t s_sym[kSumWarpThreads];
+  __shared__ uint32_t s_wsum[kEncThreads / 32];
+  __shared__ Summary s_warp[kEncThreads / 32];
+  const CodeTable* ct = &a.st->codes;
+  if (ct->maxlen > (uint32_t)kMaxLen) return;  // code construction failed; already reported
+  if (!warp_path(a.meta, a.B, ct->maxlen)) {  // uniform
+    if (threadIdx.x >= kEncThreads) return;
+    for (int s = threadIdx.x; s < 256; s += kEncThreads) s_len[s] = ct->len[s];
+    tile_sync();
+    summary_tiles(a, s_len, s_wsum, s_warp);
+    return;
+  }
+  for (int s = threadIdx.x; s < 256; s += kSumWarpThreads) s_code[s] = (uint32_t)ct->code[s];
+  // entry s of lane l at byte 256 s + 4 l
+  for (int i = threadIdx.x; i < 256 * 32; i += kSumWarpThreads) {
+    const uint32_t l = ct->len[i >> 5];
+    reinterpret_cast<uint32_t*>(s_tab)[((i >> 5) << 6) | (i & 31)] = l ? l : kLenNoCode;
+  }
+  __syncthreads();
+  bool bad = false;
+  count_warps(a, s_tab, s_code, s_sym, bad);
+  if (bad) set_error(a.st, HZ_ERR_ARG, 0x200);
 }
 
 // =================================================================== pass 2
@@ -244,24 +265,30 @@ __global__ void __launch_bounds__(kEncThreads, 4) encode_pack_kernel(EncodeArgs 
   }
 }
 
-static PerDeviceSetup<1> g_summary_setup;
+static PerDeviceSetup<2> g_summary_setup;
 
 cudaError_t launch_encode_summary(const EncodeArgs& a, int num_sms, cudaStream_t s) {
-  // dynamic shared memory for the lane-private length copies of the
-  // warp-parallel path (whether the path applies is decided on the device)
-  const int smem = a.meta ? 256 * 32 * 4 : 0;
+  // blocks of whole tiles with the metadata: the kernel that holds the
+  // warp-parallel path (whether it applies is decided on the device), with
+  // the lane-private length copies in dynamic shared memory
+  const bool warps = a.meta != nullptr && a.B % (uint32_t)kEncTile == 0;
   int per_sm = 1;
-  const cudaError_t e = launch_setup_per_device(g_summary_setup, 0, &per_sm, [&](int& out) {
-    cudaError_t r = cudaFuncSetAttribute(encode_summary_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 32 * 4);
+  const cudaError_t e = launch_setup_per_device(g_summary_setup, warps ? 1 : 0, &per_sm, [&](int& out) {
+    if (!warps)
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, encode_summary_kernel,
+                                                           kEncThreads, 0);
+    cudaError_t r = cudaFuncSetAttribute(encode_summary_warps_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSumTabBytes);
     if (r == cudaSuccess)
-      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, encode_summary_kernel, kEncThreads,
-                                                        256 * 32 * 4);
+      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, encode_summary_warps_kernel,
+                                                        kSumWarpThreads, kSumTabBytes);
     return r;
   });
   if (e != cudaSuccess) return e;
   const uint64_t grid = (uint64_t)num_sms * per_sm;
-  encode_summary_kernel<<<(unsigned)(grid < a.ntiles ? grid : a.ntiles), kEncThreads, smem, s>>>(a);
+  const unsigned g = (unsigned)(grid < a.ntiles ? grid : a.ntiles);
+  if (warps) encode_summary_warps_kernel<<<g, kSumWarpThreads, kSumTabBytes, s>>>(a);
+  else encode_summary_kernel<<<g, kEncThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -154,29 +154,36 @@ static __device__ __forceinline__ void load_tile_symbols(const EncodeArgs& a, ui
   load_symbols(a.in + g.g0, g.my_cnt, x);
 }
 
-// summary_tile with the thread's symbols already loaded.
 // The length-summing pass of the warp-parallel path: every warp of a tile on
 // its own, no CTA barrier.  Records the tile's TileMeta: each lane's bits (the
 // sum of its 32 code lengths), the warp's bits, and, for the odd runs of a
 // tile (the ones a packing item starts after), the warp's last 32 code bits
 // -- found in parallel: each lane takes one of the last lane's 32
 // symbols, a suffix sum of their lengths places its code, and the codes that
-// end within the last 32 bits are ORed together.  s_len32: the lengths kept
-// once per lane, in the lane's own bank (entry s of lane l at word 32 s + l),
-// so that 32 lanes' lookups are one shared-memory wavefront, as the
-// histogram's counters are; s_code: right-aligned codes; s_sym: 32 bytes of
-// per-warp scratch.
+// end within the last 32 bits are ORed together.  s_tab: the lengths once per
+// lane, entry s of lane l at byte 256 s + 4 l (in the lane's own bank, so
+// that 32 lanes' lookups are one shared-memory wavefront, as the histogram's
+// counters are); a 256-byte row makes a lookup's offset one byte permute of
+// the symbol byte and the lane's 4 l (bytes 128-255 of a row are not read).
+// s_code: right-aligned codes; s_sym: 32 bytes of per-warp scratch.  Warps of
+// a CTA take items (1024-symbol runs) in turn, kSumWarpThreads / 32 per CTA.
 constexpr uint32_t kLenNoCode = 1u << 16;  // > 32 codes of at most 32 bits
-static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const uint32_t* s_len32,
+constexpr int kSumWarpThreads = 512;
+constexpr int kSumTabBytes = 256 * 256;
+static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const uint8_t* s_tab,
                                                    const uint32_t* s_code, uint8_t* s_sym,
                                                    bool& bad) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // this lane's copy of the lengths: entry s at word 32 s + lane, in the lane's own bank
-  const uint32_t* my_len = s_len32 + lane;
-  constexpr uint32_t kWarps = kEncThreads / 32;
+  const uint32_t lr = lane * 4;  // byte 0 of a lookup's offset; bytes 1-3 zero
+  // the length of the symbol that selector sel moves into byte 1, for this lane
+  auto len_of = [&](uint32_t v, uint32_t sel) -> uint32_t {
+    return *reinterpret_cast<const uint32_t*>(s_tab + __byte_perm(v, lr, sel));
+  };
+  constexpr uint32_t kWarps = kEncThreads / 32;  // runs per tile
+  constexpr uint32_t kCtaWarps = kSumWarpThreads / 32;
   const uint32_t n = (uint32_t)a.n;
   const uint32_t items = a.ntiles * kWarps;
-  const uint32_t stride = gridDim.x * kWarps;
+  const uint32_t stride = gridDim.x * kCtaWarps;
   uint8_t* my_sym = s_sym + 32 * warp;
   // item it's symbols for this lane (g0, cnt); false when the warp has none
   auto geometry = [&](uint32_t it, uint32_t& g0, uint32_t& cnt) -> bool {
@@ -188,7 +195,7 @@ static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const ui
     return wlo < hi;
   };
   // the next item's symbols are loaded while the current one is summed
-  uint32_t it = blockIdx.x * kWarps + warp;
+  uint32_t it = blockIdx.x * kCtaWarps + warp;
   uint32_t g0 = 0, cnt = 0;
   bool has = it < items && geometry(it, g0, cnt);
   uint32_t x[kEncSymPerThread / 4], xn[kEncSymPerThread / 4];
@@ -208,14 +215,16 @@ static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const ui
     const uint32_t tile = it / kWarps, w = it % kWarps;
     // (static indices: x stays in registers; a byte without a code counts
     // kLenNoCode, which no sum of real lengths reaches)
+    // (selector 0x55b4: byte 0 from lr, byte 1 the symbol byte b, bytes 2-3 zero)
     uint32_t bits = 0;
     if (cnt == kEncSymPerThread) {
 #pragma unroll
-      for (int i = 0; i < kEncSymPerThread; ++i) bits += my_len[sym_of(x, i) << 5];
+      for (int i = 0; i < kEncSymPerThread; ++i)
+        bits += len_of(x[i >> 2], 0x5504u | ((uint32_t)(i & 3) << 4));
     } else {
 #pragma unroll
       for (int i = 0; i < kEncSymPerThread; ++i)
-        if ((uint32_t)i < cnt) bits += my_len[sym_of(x, i) << 5];
+        if ((uint32_t)i < cnt) bits += len_of(x[i >> 2], 0x5504u | ((uint32_t)(i & 3) << 4));
     }
     bad |= bits >= kLenNoCode;
     TileMeta& m = a.meta[tile];
@@ -234,7 +243,7 @@ static __device__ __forceinline__ void count_warps(const EncodeArgs& a, const ui
       __syncwarp();
       const uint32_t sym = my_sym[lane];
       __syncwarp();
-      const uint32_t l = my_len[sym << 5];
+      const uint32_t l = *reinterpret_cast<const uint32_t*>(s_tab + ((sym << 8) | lr));
       uint32_t suf = l;  // lengths of symbols lane .. 31
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -271,6 +280,13 @@ static __device__ __forceinline__ Summary meta_summary(const EncodeArgs& a, uint
   return starts ? Summary{1, 0, 0, total} : Summary{0, total, 0, 0};
 }
 
+// The barrier of the per-tile summary: the first kEncThreads threads of the
+// CTA (all of a kEncThreads-thread CTA; the lower half of the warp-parallel
+// summing kernel, whose other threads have left when it runs this path).
+static __device__ __forceinline__ void tile_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kEncThreads) : "memory");
+}
+
 static __device__ __forceinline__ void summary_tile_x(const EncodeArgs& a, uint32_t tile,
                                                       const uint32_t (&x)[kEncSymPerThread / 4],
                                                       const uint8_t* s_len, uint32_t* s_wsum,
@@ -301,7 +317,7 @@ static __device__ __forceinline__ void summary_tile_x(const EncodeArgs& a, uint3
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, d);
     if (lane == 0) s_wsum[warp] = bits;
-    __syncthreads();
+    tile_sync();
     if (tid == 0) {
       uint32_t total = 0;
       for (int w = 0; w < kEncThreads / 32; ++w) total += s_wsum[w];
@@ -317,14 +333,14 @@ static __device__ __forceinline__ void summary_tile_x(const EncodeArgs& a, uint3
       if (lane >= d) sm = combine(o, sm);
     }
     if (lane == 31) s_warp[warp] = sm;
-    __syncthreads();
+    tile_sync();
     if (tid == 0) {
       Summary t{0, 0, 0, 0};
       for (int w = 0; w < kEncThreads / 32; ++w) t = combine(t, s_warp[w]);
       store_summary(a.tiles[tile], t);
     }
   }
-  __syncthreads();
+  tile_sync();
 }
 
 static __device__ __forceinline__ void summary_tile(const EncodeArgs& a, uint32_t tile,

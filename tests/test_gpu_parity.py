@@ -154,6 +154,9 @@ def test_given_codes_beyond_26_and_32_bits(hz, ctx, maxlen):
     x[rng.integers(0, x.size, 2000)] = maxlen - 1
     _check_round_trip(hz, ctx, x, 1000, lengths=lens)
     _check_round_trip(hz, ctx, x, 7, lengths=lens)
+    # blocks of whole 8192-symbol tiles: the summing kernel of the warp-parallel
+    # path, which falls back to per-tile summaries for codes over 32 bits
+    _check_round_trip(hz, ctx, x, 16384, lengths=lens)
 
 
 def test_tile_start_inside_a_code_longer_than_26_bits(hz, ctx):
@@ -269,12 +272,13 @@ def test_corrupt_streams_are_rejected(hz, ctx):
     assert st == 0 and np.array_equal(y.cpu().numpy(), x)
 
 
-def test_given_code_missing_a_symbol_is_an_error(hz, ctx):
+@pytest.mark.parametrize("n,B", [(5, 4), (20_000, 8192)])
+def test_given_code_missing_a_symbol_is_an_error(hz, ctx, n, B):
     lens = np.zeros(256, dtype=np.uint8)
     lens[:2] = 1
     codes = hz.make_codes(lens, oracle.canonical_codes(lens))
-    x = torch.tensor([0, 1, 2, 1, 0], dtype=torch.uint8, device=DEV)
-    st, _, _ = _gpu_compress(hz, ctx, x, 4, codes=codes)
+    x = torch.tensor([0, 1, 2, 1, 0] * (n // 5), dtype=torch.uint8, device=DEV)
+    st, _, _ = _gpu_compress(hz, ctx, x, B, codes=codes)
     assert st == hz.HZ_ERR_ARG
 
 
