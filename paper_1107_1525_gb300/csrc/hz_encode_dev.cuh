@@ -949,6 +949,30 @@ constexpr uint32_t kPackItems = kEncThreads / 32 / kPackRuns;      // warp items
 constexpr uint32_t kWarpStageWords = kPackSyms * 32 * 16 / 32 + 8;  // codes of <= 16 bits, + alignment
 static_assert(kWarpStageWords * (kEncThreads / 32) <= (uint32_t)kEncStageWords + 4, "staging");
 
+// Bulk copies from the staging area to the output (the copy engine reads the
+// shared memory while the warp goes on packing).  The staging words are
+// written by ordinary stores: each writing thread makes them visible to the
+// copy engine (the async proxy) with a proxy fence before the copy is issued.
+static __device__ __forceinline__ void bulk_fence_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// bytes (a multiple of 16) from shared s to global g, both 16-byte aligned
+static __device__ __forceinline__ void bulk_store(void* g, const void* s, uint32_t bytes) {
+  asm volatile(
+      "cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n"
+      "cp.async.bulk.commit_group;\n" ::"l"((uint64_t)__cvta_generic_to_global(g)),
+      "r"((uint32_t)__cvta_generic_to_shared(s)), "r"(bytes)
+      : "memory");
+}
+// this thread's bulk copies have read their sources
+static __device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// this thread's bulk copies are complete
+static __device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 template <bool kWide>
 static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
   const EncodeArgs& a = sh.a;
@@ -1078,6 +1102,9 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
                (uint32_t)(2 * j + 1) < k ? sh.lent[sym_of(x, 2 * j + 1)] : 0u);
       }
     };
+    // the previous item's bulk copy has read the staging area
+    if (lane == 0) bulk_wait_read();
+    __syncwarp();
     if (cnt0) pack_run(g0, cnt0);
     if (cnt1) pack_run(g0 + kEncSymPerThread, cnt1);
     const bool first = wi == w_first;  // no word completed
@@ -1118,19 +1145,24 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
     }
     __syncwarp();
     if (kWide && direct) continue;  // (uniform) already written
-    // ---- copy out
-    for (uint32_t k = lane; 4 * k < nw + off; k += 32) {
-      const uint32_t i0 = 4 * k;
-      if (i0 >= off && i0 + 4 <= nw + off) {
-        *reinterpret_cast<uint4*>(gbase + i0) = *reinterpret_cast<const uint4*>(stw + i0);
-      } else {
-#pragma unroll
-        for (uint32_t q = 0; q < 4; ++q)
-          if (i0 + q >= off && i0 + q < nw + off) gbase[i0 + q] = stw[i0 + q];
-      }
+    // ---- copy out: staging words [off, off + nw) to gbase[off ..]; the whole
+    // 16-byte chunks [c_lo, c_hi) by one bulk copy, the up to three words
+    // before and after them by lanes 0-2 and 4-6 (all of them, at most six,
+    // when there is no whole chunk).  The next item waits for the copy to
+    // have read the staging area before it writes there.
+    const uint32_t e_w = nw + off;
+    const uint32_t c_lo = (off + 3u) & ~3u, c_hi = e_w & ~3u;
+    if (c_hi > c_lo) {
+      bulk_fence_shared();
+      __syncwarp();
+      if (lane == 0) bulk_store(gbase + c_lo, stw + c_lo, 4u * (c_hi - c_lo));
+      if (lane < c_lo - off) gbase[off + lane] = stw[off + lane];
+      else if (lane >= 4u && lane - 4u < e_w - c_hi) gbase[c_hi + lane - 4u] = stw[c_hi + lane - 4u];
+    } else if (lane < nw) {
+      gbase[off + lane] = stw[off + lane];
     }
-    __syncwarp();
   }
+  if (lane == 0) bulk_wait_all();  // (the staging area outlives no copy)
 }
 
 // Load the code table of the buffer `a` describes into the packing tables.
