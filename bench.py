@@ -44,6 +44,9 @@ WORKLOADS = {
     "mixed-256MiB": dict(n=256 * MiB, segment=64 * MiB, block=65536, sub=2048,
                          desc="256 MiB: one 64 MiB segment of each kind of the 1 GiB mix, "
                               "64 KiB blocks (profiling case)"),
+    "uniform16-1GiB": dict(n=GiB, block=65536, sub=2048,
+                           desc="1 GiB i.i.d. bytes uniform over 16 values (4-bit codes: the "
+                                "sub-block decoder takes two codes a lookup), 64 KiB blocks"),
     "zipf-1MiB": dict(n=MiB, block=4096, sub=0,
                       desc="1 MiB i.i.d. Zipf(1.1) bytes, 4 KiB blocks"),
     "field-256MiB": dict(n=1 << 28, block=16384, sub=512,
@@ -108,6 +111,8 @@ def make_input(name, device):
         return datagen.mixed_buffer(n=w["n"], segment=w["segment"], seed=2, device=device)
     if name == "zipf-1MiB":
         return datagen.zipf_buffer(w["n"], s=1.1, seed=0, device=device)
+    if name == "uniform16-1GiB":
+        return datagen.sample_iid(datagen.uniform_pmf(16), w["n"], 5, device)
     return datagen.gaussian_field_residuals(shape=(512, 512, 1024), seed=1, device=device)
 
 
@@ -221,6 +226,8 @@ def oracle_sample(name: str, sample_bytes: int):
         return torch.cat(parts).numpy(), w["block"]
     if name == "zipf-1MiB":
         return datagen.zipf_buffer(w["n"], s=1.1, seed=0).numpy(), w["block"]
+    if name == "uniform16-1GiB":
+        return datagen.sample_iid(datagen.uniform_pmf(16), sample_bytes, 5, "cpu").numpy(), w["block"]
     x = datagen.gaussian_field_residuals(shape=(64, 512, 1024), seed=1).numpy()
     return x[:sample_bytes], w["block"]
 

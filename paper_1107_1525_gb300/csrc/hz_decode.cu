@@ -106,7 +106,9 @@ static __device__ __forceinline__ void decode_sub_blocks(const DecodeArgs& a, co
     if (threadIdx.x == 0) sh.args = a;
     __syncthreads();
     const int mode = fast_mode(T, sh.c);
-    if (mode == 0 && sh.fill_k == 3) {
+    if (mode == 0 && sh.pair) {
+      sub_groups(a, u_begin, u_end, [&](uint32_t u0) { decode_units0_pair_body(u0, u_end); });
+    } else if (mode == 0 && sh.fill_k == 3) {
       sub_groups(a, u_begin, u_end, [&](uint32_t u0) { decode_units0_body<3, true>(u0, u_end); });
     } else if (mode == 0 && sh.fill_k == 4) {
       sub_groups(a, u_begin, u_end, [&](uint32_t u0) { decode_units0_body<4, true>(u0, u_end); });

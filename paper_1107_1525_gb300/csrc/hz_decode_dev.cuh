@@ -67,6 +67,9 @@ struct DecTables {
                                 // of the output pass (2, 3 or 4); 0: the general layout
   uint32_t lut_rep;             // mode 0, no code longer than 10 bits, W >= 10: lut[0, 1024)
                                 // is indexed by the top 10 bits, kept 8 times in shared memory
+  uint32_t pair;                // lut_rep, sub-block offsets and no code longer than 5 bits:
+                                // every 10-bit window holds two whole codes, and the
+                                // sub-block decoder takes two symbols a lookup
   uint32_t cnt[kMaxLen + 1];
   uint32_t offs[kMaxLen + 1];   // position in sorted[] of the first code of each length
   uint64_t first[kMaxLen + 1];  // first canonical code of each length
@@ -382,6 +385,7 @@ static __device__ void decode_setup_device(const DecodeArgs& a, DecTables* T) {
     T->lut_bits = (uint32_t)W;
     T->fill_k = mode0 ? (rep ? (maxl <= 8 ? 4u : 3u) : 2u) : 0u;
     T->lut_rep = rep ? 1u : 0u;
+    T->pair = rep && maxl <= 5 && S ? 1u : 0u;
     T->sub_S = S;
     T->sub_M = S ? B / S : 0u;
     T->units = S ? nb * (B / S) : 0u;
@@ -522,7 +526,7 @@ static_assert((1u << kLutMaxBits) + kL2Entries / 2 <= kFastLutWords, "table area
 
 struct FastShared {
   uint32_t lut[kFastLutWords];
-  uint32_t has_l2, fill_k, lut_rep;
+  uint32_t has_l2, fill_k, lut_rep, pair;
   uint32_t sub_S, sub_M, units;  // sub-block offsets (sub_M = 0: none)
   CanonTables c;
   // the launch's arguments (the stream being decoded), for the sub-block
@@ -559,8 +563,20 @@ static __device__ __forceinline__ uint32_t fast_ring_word() {
 static __device__ __forceinline__ void load_fast_tables(FastShared& sh, const DecTables* T,
                                                         int tid, int nt) {
   const int W = (int)T->lut_bits;
-  const uint32_t lut_rep = T->lut_rep;
-  if (lut_rep) {
+  const uint32_t lut_rep = T->lut_rep, pair = T->pair;
+  if (lut_rep && pair) {
+    // the pair layout: entry u (copy c at word 8u + c) holds the two codes
+    // that start the 10-bit value u -- the second is fixed by the 10 - l1 >= 5
+    // bits after the first, as no code is longer than 5 bits:
+    // l1 + l2 | l1 << 8 | s1 << 16 | s2 << 24
+    for (int i = tid; i < (int)kFastLutWords; i += nt) {
+      const uint32_t u = (uint32_t)i >> 3;
+      const uint32_t e1 = T->lut[u] >> 16;  // l1 | s1 << 8
+      const uint32_t l1 = e1 & 31u;
+      const uint32_t e2 = T->lut[(u << l1) & 1023u] >> 16;
+      sh.lut[i] = (l1 + (e2 & 31u)) | (l1 << 8) | ((e1 >> 8) << 16) | ((e2 >> 8) << 24);
+    }
+  } else if (lut_rep) {
     for (int i = tid; i < (int)kFastLutWords; i += nt) sh.lut[i] = T->lut[i >> 3];
   } else {
     for (int i = tid; i < (1 << W); i += nt) sh.lut[i] = T->lut[i];
@@ -575,6 +591,7 @@ static __device__ __forceinline__ void load_fast_tables(FastShared& sh, const De
     sh.has_l2 = has_l2;
     sh.fill_k = T->fill_k;
     sh.lut_rep = lut_rep;
+    sh.pair = pair;
     sh.sub_S = T->sub_S;
     sh.sub_M = T->sub_M;
     sh.units = T->units;
@@ -1414,9 +1431,89 @@ __device__ __forceinline__ void decode_units0_body(uint32_t u0, uint32_t u_end) 
   if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x330);
 }
 
+// Mode 0 with the pair layout (no code longer than 5 bits): two codes per
+// lookup in the 32-symbol groups -- a step consumes at most 10 bits, so a
+// fill every 3 steps, counted over the group's 16 steps; the group's words
+// take one byte permute each (bytes 2 and 3 of two entries).  The bytes before
+// the first 32-byte boundary and after the last group take one code a step
+// (the entry's first code, its length in bits 8-12).
+static __device__ __forceinline__ void decode_units0_pair_body(uint32_t u0, uint32_t u_end) {
+  FastShared& sh = fast_sh();
+  const DecodeArgs& a = sh.args;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t cw = lane & 7u;  // the lane's copy of the table
+  const uint32_t u = u0 + lane;
+  SubRange r;
+  r.ok = true;
+  r.count = 0;
+  r.out_at = 0;
+  if (u < u_end) r = sub_range(a, sh.c, sh.sub_S, sh.sub_M, u);
+  bool bad = !r.ok;
+  uint32_t rem = r.ok ? r.count : 0u;
+  uint8_t* dst = a.out + r.out_at;
+  RingWin w;
+  auto entry = [&]() -> uint32_t { return sh.lut[((w.bh >> 22) << 3) | cw]; };
+  // one code: its symbol, the buffer advanced by its length
+  auto step1 = [&]() -> uint8_t {
+    const uint32_t h = entry();
+    w.take0((h >> 8) & 31u);
+    return (uint8_t)(h >> 16);
+  };
+  // two codes: the entry (symbols in bytes 2 and 3), the buffer advanced by
+  // both lengths (bits 8 and up drop out of the bit count's low byte)
+  auto step2 = [&]() -> uint32_t {
+    const uint32_t h = entry();
+    w.take0(h);
+    return h;
+  };
+  if (rem) {
+    w.setup(r.payload, a.in + a.in_len);
+    w.init0(r.start);
+    while (rem && (((uintptr_t)dst) & 31)) {
+      if ((((uintptr_t)dst) & 7) == 0) w.refill<false>();
+      w.fill0();
+      *dst++ = step1();
+      --rem;
+    }
+  }
+  while (__any_sync(0xFFFFFFFFu, rem >= 32)) {
+    if (rem >= 32) {
+      uint32_t q[8];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        w.refill<false>();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int s = 8 * half + 2 * j;  // the group's step
+          if (s % 3 == 0) w.fill0();
+          const uint32_t ha = step2();
+          if ((s + 1) % 3 == 0) w.fill0();
+          const uint32_t hb = step2();
+          q[4 * half + j] = __byte_perm(ha, hb, 0x7632u);
+        }
+      }
+      st_global_v8(dst, q);
+      dst += 32;
+      rem -= 32;
+    }
+  }
+  while (rem) {
+    if ((rem & 7) == 0) w.refill<false>();
+    w.fill0();
+    *dst++ = step1();
+    --rem;
+  }
+  if (r.ok && r.count) bad = w.pos0() != r.end;
+  cp_async_wait<0>();  // nothing of this warp's units may land in the ring after we leave
+  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(a.st, HZ_ERR_CORRUPT, 0x332);
+}
+
 template <int K2, bool kRep>
 __device__ __noinline__ void decode_units_warp0(uint32_t u0, uint32_t u_end) {
   decode_units0_body<K2, kRep>(u0, u_end);
+}
+static __device__ __noinline__ void decode_units_warp0_pair(uint32_t u0, uint32_t u_end) {
+  decode_units0_pair_body(u0, u_end);
 }
 
 // Modes 1 and 2 (see decode_block_warp): one code per step from the general
@@ -1487,7 +1584,8 @@ __device__ __noinline__ void decode_units_warp(uint32_t u0, uint32_t u_end) {
 // capped at u_end, in the stream's mode.
 static __device__ __forceinline__ void decode_units_fast(uint32_t u0, uint32_t u_end, int mode) {
   if (mode == 0) {
-    if (fast_sh().fill_k == 4) decode_units_warp0<4, true>(u0, u_end);
+    if (fast_sh().pair) decode_units_warp0_pair(u0, u_end);
+    else if (fast_sh().fill_k == 4) decode_units_warp0<4, true>(u0, u_end);
     else if (fast_sh().fill_k == 3) decode_units_warp0<3, true>(u0, u_end);
     else decode_units_warp0<2, false>(u0, u_end);
   } else if (mode == 1) decode_units_warp<1>(u0, u_end);

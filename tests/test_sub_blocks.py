@@ -12,7 +12,7 @@ import torch
 import datagen
 import oracle
 from tests import format_reader
-from tests.test_decode_modes import CODES, _chain, _sample
+from tests.test_decode_modes import CODES, _chain, _flat, _sample
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -121,6 +121,85 @@ def test_sub_block_runs_of_long_codes(hz, maxlen, B, S):
     st, y = _decode(hz, ctx, torch.from_numpy(want).to(DEV), n)
     assert st == 0 and torch.equal(y, xd)
     ctx.close()
+
+
+def _mixed5() -> np.ndarray:
+    """A complete code of 1- to 5-bit lengths over 8 symbols spread over the
+    byte range (1/2 + 1/4 + 2/16 + 4/32 = 1)."""
+    lengths = np.zeros(256, dtype=np.uint8)
+    for s, l in zip((9, 200, 31, 32, 120, 121, 122, 255), (1, 2, 4, 4, 5, 5, 5, 5)):
+        lengths[s] = l
+    return lengths
+
+
+@pytest.mark.parametrize("name", ["chain5", "flat4x16", "flat5x32", "mixed5", "chain2"])
+@pytest.mark.parametrize("B,S", [(65536, 2048), (16384, 512), (4096, 32)])
+def test_sub_block_two_codes_a_lookup(hz, name, B, S):
+    """No code longer than 5 bits: every 10-bit window holds two whole codes,
+    and the sub-block decoder takes two symbols a lookup (in 32-symbol groups;
+    one a step before a lane's first 32-byte boundary and after its last
+    group).  Ragged lengths, uniform and skewed symbols, runs of the longest
+    codes across sub-block boundaries, and the oracle's stream decoded too."""
+    lengths = {"chain5": _chain(5), "flat4x16": _flat(4, 16), "flat5x32": _flat(5, 32),
+               "mixed5": _mixed5(), "chain2": _chain(2)}[name]
+    codes = hz.make_codes(lengths, oracle.canonical_codes(lengths))
+    ctx = _ctx(hz, S)
+    syms = np.nonzero(lengths)[0]
+    longest = syms[lengths[syms] == lengths.max()]
+    rng = np.random.default_rng(B + S)
+    for n in (3 * B + 5 * S + 29, 2 * B, S + 1, 31):
+        x = _sample(lengths, n, n + S)
+        for at in (0, S - 7, n - 40):
+            if 0 <= at < n:
+                x[at:at + 40] = longest[rng.integers(0, len(longest), len(x[at:at + 40]))]
+        xd = torch.from_numpy(x).to(DEV)
+        s = hz.compress(xd, B, ctx=ctx, codes=codes)
+        want = oracle.compress(x, B, lengths=lengths, sub=S)
+        assert np.array_equal(s.cpu().numpy(), want), (name, B, S, n)
+        st, y = _decode(hz, ctx, s, n)
+        assert st == 0 and torch.equal(y, xd), (name, B, S, n)
+        # the output at an offset that is not 32-byte aligned (one code a step
+        # up to the first boundary)
+        out = torch.empty(n + 5, dtype=torch.uint8, device=DEV)
+        ol = torch.zeros(1, dtype=torch.int64, device=DEV)
+        hz.hz_decompress(ctx, s, s.numel(), out[5:], n, ol)
+        assert hz.hz_sync(ctx) == 0 and torch.equal(out[5:], xd), (name, B, S, n)
+    # a flipped payload bit is caught by the sub-block's end check or decodes to
+    # other bytes (never the input)
+    x = _sample(lengths, 4 * B, 7)
+    xd = torch.from_numpy(x).to(DEV)
+    s = hz.compress(xd, B, ctx=ctx, codes=codes)
+    bad = s.clone()
+    at = s.numel() - 100
+    bad[at] ^= 0x10
+    st, y = _decode(hz, ctx, bad, x.size)
+    assert st == hz.HZ_ERR_CORRUPT or not torch.equal(y, xd)
+    st, y = _decode(hz, ctx, s, x.size)
+    assert st == 0 and torch.equal(y, xd)
+    ctx.close()
+
+
+def test_sub_block_two_codes_a_lookup_in_batches(hz):
+    """The batched decoder's path for the same streams."""
+    ctx = hz.Context(0)
+    ctx_sub = _ctx(hz, 512)
+    streams, bufs = [], []
+    for i, name in enumerate(["chain5", "flat4x16", "mixed5", "chain2"] * 3):
+        lengths = {"chain5": _chain(5), "flat4x16": _flat(4, 16), "mixed5": _mixed5(),
+                   "chain2": _chain(2)}[name]
+        codes = hz.make_codes(lengths, oracle.canonical_codes(lengths))
+        x = torch.from_numpy(_sample(lengths, 50_000 + 7919 * i, i)).to(DEV)
+        streams.append(hz.compress(x, 16384, ctx=ctx_sub, codes=codes).clone())
+        bufs.append(x)
+    outs = [torch.empty(x.numel(), dtype=torch.uint8, device=DEV) for x in bufs]
+    reqs = [(hz.HZ_OP_DECOMPRESS, 0, s, s.numel(), o, o.numel()) for s, o in zip(streams, outs)]
+    t = hz.hz_submit(ctx, reqs)
+    st, per, lens = hz.hz_poll(ctx, t, len(reqs), -1)
+    assert st == 0 and (per == 0).all()
+    for x, o in zip(bufs, outs):
+        assert torch.equal(x, o)
+    ctx.close()
+    ctx_sub.close()
 
 
 @pytest.mark.parametrize("threads", [128, 256])
