@@ -251,10 +251,11 @@ __global__ void __launch_bounds__(kEncThreads, 4) encode_pack_kernel(EncodeArgs 
   pack_load_tables(sh, a);
   __syncthreads();
   // every tile inside one record and codes of at most 32 bits: warps pack on
-  // their own, from the tile metadata of the length-summing pass (two codes
-  // a step when no code is longer than 16 bits)
+  // their own, from the tile metadata of the length-summing pass (four codes
+  // a step when no code is longer than 8 bits, two when none is longer than 16)
   if (warp_path(a.meta, a.B, maxlen)) {
-    if (maxlen <= 16) pack_warps_fast<false>(sh);
+    if (maxlen <= 8) pack_warps_fast<false, true>(sh);
+    else if (maxlen <= 16) pack_warps_fast<false>(sh);
     else pack_warps_fast<true>(sh);
     return;
   }

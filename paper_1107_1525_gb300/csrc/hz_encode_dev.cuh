@@ -973,7 +973,7 @@ static __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-template <bool kWide>
+template <bool kWide, bool kQuad = false>
 static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
   const EncodeArgs& a = sh.a;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1079,6 +1079,23 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
         nacc ^= 32u;
       }
     };
+    // Four codes of at most 8 bits a step: two pairs joined as above, the
+    // second shifted by the first pair's length (ea + eb: its low five bits
+    // are la + lb <= 16), then pushed as one code of at most 32 bits.
+    auto push4 = [&](uint32_t ea, uint32_t eb, uint32_t ec, uint32_t ed) {
+      const uint32_t cab = (ea & ~31u) | __funnelshift_r(eb & ~31u, 0u, ea);
+      const uint32_t ccd = (ec & ~31u) | __funnelshift_r(ed & ~31u, 0u, ec);
+      const uint32_t eab = ea + eb;
+      const uint32_t cw = cab | __funnelshift_r(ccd, 0u, eab);  // ccd >> (la + lb)
+      const uint32_t over = __funnelshift_r(0u, cw, nacc);       // cw << (32 - nacc)
+      acc_hi |= __funnelshift_r(cw, 0u, nacc);                   // cw >> nacc
+      nacc += eab + ec + ed;
+      if (nacc & 32u) {
+        emit(acc_hi);
+        acc_hi = over;
+        nacc ^= 32u;
+      }
+    };
     // one 32-symbol run at g (k symbols of it)
     auto pack_run = [&](uint32_t g, uint32_t k) {
       uint32_t x[kEncSymPerThread / 4];
@@ -1091,6 +1108,11 @@ static __device__ __forceinline__ void pack_warps_fast(PackShared& sh) {
             push1(e.x, e.y);
           }
         }
+      } else if (kQuad && k == (uint32_t)kEncSymPerThread) {
+#pragma unroll
+        for (int j = 0; j < kEncSymPerThread / 4; ++j)
+          push4(sh.lent[sym_of(x, 4 * j)], sh.lent[sym_of(x, 4 * j + 1)],
+                sh.lent[sym_of(x, 4 * j + 2)], sh.lent[sym_of(x, 4 * j + 3)]);
       } else if (k == (uint32_t)kEncSymPerThread) {
 #pragma unroll
         for (int j = 0; j < kEncSymPerThread / 2; ++j)
