@@ -72,10 +72,12 @@ __host__ __device__ __forceinline__ bool warp_path(const TileMeta* meta, uint32_
   return meta != nullptr && B % (uint32_t)kEncTile == 0 && maxlen <= 32;
 }
 
-// The encoder's tile scan runs in CTAs of kScanTilesPerCta tiles; n < 2^32
-// bounds their number.
+// The encoder's tile scan runs in CTAs of kScanCtaTiles tiles (one a
+// thread); n < 2^32 bounds their number.  The batched scan (one CTA a buffer)
+// walks a buffer's tiles in chunks of kScanTilesPerCta.
+constexpr int kScanCtaTiles = 1024;
 constexpr int kScanTilesPerCta = 4096;
-constexpr int kMaxScanCtas = (int)((1ull << 32) / kEncTile / kScanTilesPerCta);  // 128
+constexpr int kMaxScanCtas = (int)((1ull << 32) / kEncTile / kScanCtaTiles);  // 512
 
 struct DevState {
   uint32_t error;           // first error recorded (as -hz_status), 0 = none
@@ -88,10 +90,12 @@ struct DevState {
   uint32_t tile_counter;    // ticket of the scan CTAs
   uint32_t enc_ok;          // set by the encoder's scan: 1 when the stream fits the output
   uint32_t hist[256];
-  uint32_t scan_flags[kMaxScanCtas];  // 1 = aggregate published, 2 = inclusive prefix
+  // 1 = aggregate published, 2 = inclusive prefix (one spare entry: with the
+  // scan-stall injection the tickets run from 1 to the CTA count)
+  uint32_t scan_flags[kMaxScanCtas + 1];
   // ---- not cleared
   CodeTable codes;
-  TileStatus scan_aux[kMaxScanCtas];  // per scan CTA: aggregate and inclusive prefix
+  TileStatus scan_aux[kMaxScanCtas + 1];  // per scan CTA: aggregate and inclusive prefix
 };
 
 // ------------------------------------------------------------ PTX helpers

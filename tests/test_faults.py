@@ -34,7 +34,7 @@ def _compress_status(hz, ctx, x, B):
     return hz.hz_sync(ctx)
 
 
-@pytest.mark.parametrize("n", [5 * MiB + 3, 40 * MiB + 17])  # one scan CTA, and two
+@pytest.mark.parametrize("n", [5 * MiB + 3, 40 * MiB + 17])  # one scan CTA, and six
 def test_scan_wait_runs_out_and_the_context_recovers(hz, n):
     ctx = hz.Context(0)
     ctx.set_option(hz.HZ_OPT_SPIN_LIMIT, 4000)
