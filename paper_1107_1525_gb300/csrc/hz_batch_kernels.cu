@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) batch_decode_kernel(BatchCtl*
     const BatchDecomp& d = decomps[i];
     const DecTables* T = d.T;
     if (i != cur) {
-      load_fast_tables(sh, T, threadIdx.x, kFastThreads);
+      load_fast_tables<false>(sh, T, threadIdx.x, kFastThreads);
       if (threadIdx.x == 0) sh.args = decomp_args(d);
       cur = i;
       __syncthreads();

@@ -102,7 +102,7 @@ static __device__ __forceinline__ void decode_sub_blocks(const DecodeArgs& a, co
   const uint32_t u_begin = a.k_begin * M, u_end = k_end > a.k_begin ? k_end * M : u_begin;
   if (u_begin + 32 * blockIdx.x * warps < u_end) {  // uniform: this CTA has work
     FastShared& sh = fast_sh();
-    load_fast_tables(sh, T, threadIdx.x, blockDim.x);
+    load_fast_tables<true>(sh, T, threadIdx.x, blockDim.x);
     if (threadIdx.x == 0) sh.args = a;
     __syncthreads();
     const int mode = fast_mode(T, sh.c);
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) decode_fast_kernel(DecodeArgs
   const bool spread = k_end - a.k_begin < gridDim.x * warps;
   const uint32_t k0 = a.k_begin + (spread ? warp * gridDim.x + blockIdx.x : blockIdx.x * warps + warp);
   FastShared& sh = fast_sh();
-  load_fast_tables(sh, T, threadIdx.x, blockDim.x);
+  load_fast_tables<true>(sh, T, threadIdx.x, blockDim.x);
   __syncthreads();
   const int mode = fast_mode(T, sh.c);
   const uint32_t stride = gridDim.x * warps;

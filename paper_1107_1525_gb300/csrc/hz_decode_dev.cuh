@@ -560,10 +560,15 @@ static __device__ __forceinline__ uint32_t fast_ring_word() {
 }
 
 // The lookup tables of T into shared memory (all threads of the CTA).
+// kPair: the caller decodes streams in the pair layout two codes a lookup
+// (the single-stream kernel); otherwise their tables load as plain mode-0
+// tables (the batched kernel, whose other decode functions keep their
+// registers without that path).
+template <bool kPair>
 static __device__ __forceinline__ void load_fast_tables(FastShared& sh, const DecTables* T,
                                                         int tid, int nt) {
   const int W = (int)T->lut_bits;
-  const uint32_t lut_rep = T->lut_rep, pair = T->pair;
+  const uint32_t lut_rep = T->lut_rep, pair = kPair ? T->pair : 0u;
   if (lut_rep && pair) {
     // the pair layout: entry u (copy c at word 8u + c) holds the two codes
     // that start the 10-bit value u -- the second is fixed by the 10 - l1 >= 5
@@ -1512,9 +1517,6 @@ template <int K2, bool kRep>
 __device__ __noinline__ void decode_units_warp0(uint32_t u0, uint32_t u_end) {
   decode_units0_body<K2, kRep>(u0, u_end);
 }
-static __device__ __noinline__ void decode_units_warp0_pair(uint32_t u0, uint32_t u_end) {
-  decode_units0_pair_body(u0, u_end);
-}
 
 // Modes 1 and 2 (see decode_block_warp): one code per step from the general
 // table; longer codes through the second-level table or from memory.
@@ -1581,11 +1583,11 @@ __device__ __noinline__ void decode_units_warp(uint32_t u0, uint32_t u_end) {
 }
 
 // Units [u0, u0 + 32) of the stream whose arguments are in fast_sh().args,
-// capped at u_end, in the stream's mode.
+// capped at u_end, in the stream's mode (not the pair layout: the
+// single-stream kernel decodes that inline).
 static __device__ __forceinline__ void decode_units_fast(uint32_t u0, uint32_t u_end, int mode) {
   if (mode == 0) {
-    if (fast_sh().pair) decode_units_warp0_pair(u0, u_end);
-    else if (fast_sh().fill_k == 4) decode_units_warp0<4, true>(u0, u_end);
+    if (fast_sh().fill_k == 4) decode_units_warp0<4, true>(u0, u_end);
     else if (fast_sh().fill_k == 3) decode_units_warp0<3, true>(u0, u_end);
     else decode_units_warp0<2, false>(u0, u_end);
   } else if (mode == 1) decode_units_warp<1>(u0, u_end);

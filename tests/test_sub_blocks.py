@@ -180,7 +180,8 @@ def test_sub_block_two_codes_a_lookup(hz, name, B, S):
 
 
 def test_sub_block_two_codes_a_lookup_in_batches(hz):
-    """The batched decoder's path for the same streams."""
+    """The same streams through the batched decoder (which takes them one code
+    a lookup, from the plain mode-0 tables)."""
     ctx = hz.Context(0)
     ctx_sub = _ctx(hz, 512)
     streams, bufs = [], []
