@@ -56,13 +56,13 @@ WORKLOADS = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # ncu captures on the 256 MiB profiling case, scaled by the units processed to a
 # 1 GiB launch (profiles/*.md).  Each figure holds only for the kernel sources
-# it was measured on: "digest" is kernel_digest(kernel) of the files that
-# kernel is compiled from, and the line reports null traffic when they have
-# changed since.
+# it was measured on: "digest" is kernel_digest(kernel) of the code of the
+# files that kernel is compiled from, and the line reports null traffic when
+# that code has changed since.
 NCU_TRAFFIC = {"mixed-1GiB": {"sub_block": 2048,
-                              "decode": {"digest": "b3742a37ab95c2e5",
+                              "decode": {"digest": "ad95f21b550ef3e4",
                                          "bytes": 4 * (231538688 + 233258496)},
-                              "encode_pack": {"digest": "217103361711fe58",
+                              "encode_pack": {"digest": "cdbe728af2374975",
                                               "bytes": 4 * (288471040 + 167254016)}}}
 # the files each kernel is compiled from (its translation unit and headers)
 KERNEL_SOURCES = {
@@ -75,9 +75,19 @@ KERNEL_SOURCES = {
 }
 
 
+def source_code_only(text: str) -> str:
+    """C/CUDA source without its comments, trailing blanks and empty lines (the
+    sources hold no comment markers inside string literals)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def kernel_digest(kernel=None) -> str:
-    """SHA-256 (first 16 hex digits) over the CUDA sources `kernel` is compiled
-    from (KERNEL_SOURCES), or over all of the library's CUDA sources."""
+    """SHA-256 (first 16 hex digits) over the code of the CUDA sources `kernel`
+    is compiled from (KERNEL_SOURCES), or of all of the library's CUDA
+    sources; comments do not count (source_code_only)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1107_1525_gb300", "csrc")
     files = KERNEL_SOURCES.get(kernel) or sorted(
@@ -85,8 +95,8 @@ def kernel_digest(kernel=None) -> str:
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.basename(f).encode())
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(source_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

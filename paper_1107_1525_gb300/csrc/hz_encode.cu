@@ -7,22 +7,24 @@
 // back, so a record's position depends on the sizes of all earlier records.
 //
 // Three launches, no inter-CTA waiting:
-//   1. encode_summary_kernel -- the length-summing pass: every 8192-symbol
-//      tile is reduced to a Summary (below) of its code lengths and record
-//      starts;
+//   1. encode_summary_warps_kernel / encode_summary_kernel -- the
+//      length-summing pass: per-warp counts and tails for the warp-parallel
+//      path, else every 8192-symbol tile reduced to a Summary (below) of its
+//      code lengths and record starts;
 //   2. encode_scan_kernel -- one CTA scans the tile summaries into each
 //      tile's start state (word position of the open record, bits already in
 //      it), fixes the stream size and checks it against the output capacity;
 //   3. encode_pack_kernel -- every tile is packed independently from its
-//      start state (when every tile lies inside one record and no code is
+//      start state.  When every tile lies inside one record and no code is
 //      longer than 32 bits, warps pack 2048-symbol items on their own from
-//      the summing pass's per-thread bit counts: pack_warps_fast; otherwise
-//      per tile): each thread packs 32 consecutive symbols MSB-first with a
-//      64-bit shift accumulator (two codes per step when codes have at most
-//      16 bits), the tile's words are staged in shared memory (atomicOr only
-//      for a word split between two threads) and written out with 16-byte
-//      stores.  Tiles run last-to-first so the first ones packed are those the
-//      length-summing pass read last, still in L2.
+//      the summing pass's per-thread bit counts (pack_warps_fast: a 32-bit
+//      accumulator per lane, words staged per warp and copied out by bulk
+//      copies).  Otherwise per tile: each thread packs 32 consecutive symbols
+//      MSB-first with a 64-bit shift accumulator (two codes per step when
+//      codes have at most 16 bits), the tile's words are staged in shared
+//      memory (atomicOr only for a word split between two threads) and
+//      written out with 16-byte stores.  Tiles run last-to-first so the first
+//      ones packed are those the length-summing pass read last, still in L2.
 // A word split between two tiles is written by the later tile, which
 // re-derives the earlier tile's last (< 32) bits from the input; the
 // delimiter of a record is written by the tile holding the record's last

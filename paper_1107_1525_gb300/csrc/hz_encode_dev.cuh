@@ -917,7 +917,7 @@ __device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, co
 
 // ------------------------------------------------- warp-parallel packing
 // Tiles that lie inside one record (B a multiple of the tile), codes of at
-// most 16 bits, with the TileMeta the length-summing pass wrote: a warp packs
+// most 32 bits, with the TileMeta the length-summing pass wrote: a warp packs
 // 2048 symbols of a tile (two of the summing pass's 1024-symbol runs) on its
 // own, with no CTA barrier.
 //   - lane l takes the 64 symbols of the summing pass's 32-symbol runs 2l and
@@ -925,8 +925,9 @@ __device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, co
 //     scanned with shuffles, the warp's own offset within the tile and the
 //     tile's start state come from the metadata and the tile scan;
 //   - a lane packs its symbols two codes at a time (a pair is at most 32
-//     bits) into a 64-bit accumulator and writes each word it completes into
-//     the warp's staging area in shared memory;
+//     bits; four at a time when no code is longer than 8 bits) into one
+//     32-bit accumulator and writes each word it completes into the warp's
+//     staging area in shared memory;
 //   - the word a lane shares with the lane before it (its first word, when it
 //     starts mid-word) gets that lane's partial last word through one shuffle;
 //     a warp's first word gets the previous run's last bits from the
@@ -934,7 +935,8 @@ __device__ __noinline__ void pack_tile_general(PackShared& sh, uint32_t tile, co
 //     the tile before);
 //   - a lane's partial last word belongs to the next lane (or warp), except
 //     at the end of the record, where it is written zero-padded;
-//   - the warp copies its words out with 16-byte stores.
+//   - the item's whole 16-byte chunks leave the staging area by one bulk
+//     copy (cp.async.bulk), the ragged words at its ends by lanes' stores.
 // No word is written twice and the output needs no clearing.  Taking 64
 // symbols a lane halves the per-lane work that does not depend on the symbol
 // count (offsets, shuffles, the shared words, the copy-out).
