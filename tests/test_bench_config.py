@@ -54,3 +54,12 @@ def test_kernel_digest_covers_each_kernels_sources():
         d = bench.kernel_digest(kernel)
         assert len(d) == 16 and d == bench.kernel_digest(kernel)
     assert bench.kernel_digest("decode") != bench.kernel_digest("encode_pack")
+
+
+def test_digest_ignores_comments_only():
+    a = "int f(int x) {  // one\n  return x + 1; /* two\n three */\n}\n"
+    b = "int f(int x) {\n\n  return x + 1;\n}  // other words\n"
+    c = "int f(int x) {\n  return x + 2;\n}\n"
+    assert bench.source_code_only(a) == bench.source_code_only(b)
+    assert bench.source_code_only(a) != bench.source_code_only(c)
+    assert "return x + 1;" in bench.source_code_only(a)
